@@ -1,0 +1,99 @@
+"""Pins of the whole oracle against analytic flows and the paper's observed orders.
+
+Sec. 3.1 of arXiv:1712.08288 reports convergence orders "around 2" for the five
+l-rules on the Poiseuille channel (its plots are not available, only this statement);
+Sec. 3.3 reports second order for the pipe.  The circular Couette flow is the
+textbook steady solution u_theta = U1 R1 (R2^2/r - r)/(R2^2 - R1^2).
+"""
+
+import numpy as np
+import pytest
+
+from oracle import lattices as L
+from oracle import lbm as O
+from paper_1712_08288_gb300 import workloads as W
+
+RULES = {"g": (0, 1, 0), "1.5g": (0, 1.5, 0), "2g": (0, 2, 0), "g2": (0, 0, 1), "g2+g": (0, 1, 1)}
+
+
+def run_to_steady(sim, tol, chunk=200, max_steps=200000):
+    """Step until ||u^t - u^(t-chunk)|| / ||u^t|| < tol."""
+    _, u0 = sim.moments()
+    steps = 0
+    while steps < max_steps:
+        sim.step(chunk)
+        steps += chunk
+        _, u1 = sim.moments()
+        res = np.sqrt(np.nansum((u1 - u0) ** 2) / np.nansum(u1 ** 2))
+        u0 = u1
+        if res < tol:
+            return steps
+    raise AssertionError("no steady state")
+
+
+def observed_order(sizes, errors):
+    """Least-squares slope of log(error) against log(1/size)."""
+    return -np.polyfit(np.log(sizes), np.log(errors), 1)[0]
+
+
+def poiseuille_error(Ny, gamma, s_nu, rule, b=1.0):
+    w = W.poiseuille_2d(Ny, gamma, s_nu)
+    sim = O.Simulation(L.D2Q9, w["shape"], w["S"], w["rho0"], w["solid"], w["links"],
+                       scheme=RULES[rule] + (b,), force=w["force"])
+    sim.init_equilibrium(None, np.nan_to_num(w["u_exact"])[:, :2])
+    run_to_steady(sim, 1e-11)
+    _, u = sim.moments()
+    return O.relative_l2_error(w["u_exact"][:, :2], u[:, :2], ~w["solid"])
+
+
+@pytest.mark.parametrize("rule,gamma,s_nu", [
+    ("g", 0.25, 1.0), ("1.5g", 0.75, 1.0), ("2g", 1.0, 1.0), ("g2", 0.25, 1.5),
+    ("g2+g", 0.75, 0.5), ("g", 0.75, 1.5)])
+def test_poiseuille_second_order(rule, gamma, s_nu):
+    """Sec. 3.1: N_y = 11, 21, 41, h = H/(N_y - 2 + 2 gamma): observed order ~2."""
+    sizes = [11, 21, 41]
+    errs = [poiseuille_error(n, gamma, s_nu, rule) for n in sizes]
+    inv_h = [n - 2 + 2 * gamma for n in sizes]      # 1/h with H = 1
+    p = observed_order(inv_h, errs)
+    assert 1.85 < p < 2.4, (errs, p)
+
+
+def test_b_scheme_is_second_order():
+    """Eq. (2.13) with b < 1 keeps second order (Sec. 2, last paragraph)."""
+    sizes = [11, 21, 41]
+    errs = [poiseuille_error(n, 0.25, 1.0, "g", b=0.6) for n in sizes]
+    inv_h = [n - 1.5 for n in sizes]
+    assert 1.85 < observed_order(inv_h, errs) < 2.4, errs
+
+
+def test_couette_curved_walls_order():
+    """Circular Couette flow (64^2 problem scaled by n/64, diffusive scaling):
+    observed order >= 1.9 on curved walls."""
+    sizes = [32, 48, 64]
+    errs = []
+    for n in sizes:
+        w = W.couette_config(n)
+        sim = O.Simulation(L.D2Q9, w["shape"], w["S"], w["rho0"], w["solid"], w["links"],
+                           scheme=(0, 1, 0, 1.0))
+        sim.init_equilibrium(None, np.nan_to_num(w["u_exact"])[:, :2])
+        run_to_steady(sim, 1e-9)
+        _, u = sim.moments()
+        errs.append(O.relative_l2_error(w["u_exact"][:, :2], u[:, :2], ~w["solid"]))
+    assert errs[-1] < 5e-3
+    assert observed_order(sizes, errs) >= 1.9, errs
+
+
+@pytest.mark.slow
+def test_tilted_pipe_order_d3q19():
+    """Hagen-Poiseuille flow in a pipe tilted off the lattice axes (skewed periodic
+    wrap), D3Q19: error falls by ~4 from L = 16 to L = 32 (Sec. 3.3: second order)."""
+    errs = []
+    for Lb in (16, 32):
+        w = W.tilted_pipe_3d(Lb)
+        sim = O.Simulation(L.D3Q19, w["shape"], w["S"], w["rho0"], w["solid"], w["links"],
+                           scheme=(0, 1, 0, 1.0), force=w["force"], skew=w["skew"])
+        sim.init_equilibrium(None, np.nan_to_num(w["u_exact"]))
+        run_to_steady(sim, 1e-8, chunk=100)
+        _, u = sim.moments()
+        errs.append(O.relative_l2_error(w["u_exact"], u, ~w["solid"]))
+    assert 1.85 < np.log2(errs[0] / errs[1]) < 2.3, errs

@@ -1,0 +1,92 @@
+"""The input generators: wall fractions against bisection on the exact surfaces,
+cut-link completeness, seeded reproducibility."""
+
+import numpy as np
+
+from paper_1712_08288_gb300 import workloads as W
+
+
+def _bisect(inside_solid, p, d, lo=0.0, hi=1.0, it=80):
+    """First crossing of the wall along p + t d, t in (0, 1] (p fluid, p + d solid)."""
+    for _ in range(it):
+        mid = 0.5 * (lo + hi)
+        if inside_solid(p + mid * d):
+            hi = mid
+        else:
+            lo = mid
+    return hi
+
+
+def test_couette_fractions_by_bisection():
+    w = W.couette_2d(40, (20.3, 19.6), 6.2, 17.5, 0.01)
+    E = W.DIRECTIONS["D2Q9"].astype(float)
+    c = np.array([20.3, 19.6, 0.0])
+
+    def solid(p):
+        r = np.hypot(p[0] - c[0], p[1] - c[1])
+        return not (6.2 < r < 17.5)
+    L = w["links"]
+    nx = 40
+    for k in range(0, len(L["node"]), 7):
+        n = L["node"][k]
+        p = np.array([n % nx, n // nx, 0.0])
+        q = _bisect(solid, p, E[L["d"][k]])
+        assert abs(q - L["q"][k]) < 1e-12
+
+
+def test_couette_wall_velocity_is_tangential():
+    U1, R1 = 0.02, 6.2
+    w = W.couette_2d(40, (20.3, 19.6), R1, 17.5, U1)
+    L = w["links"]
+    E = W.DIRECTIONS["D2Q9"].astype(float)
+    nx = 40
+    for k in range(len(L["node"])):
+        n = L["node"][k]
+        xb = np.array([n % nx, n // nx, 0.0]) + L["q"][k] * E[L["d"][k]] - [20.3, 19.6, 0]
+        uw = L["uw"][k]
+        if np.hypot(*xb[:2]) < 10:          # inner wall
+            assert abs(np.hypot(*xb[:2]) - R1) < 1e-9
+            assert abs(np.linalg.norm(uw) - U1) < 1e-12
+            assert abs(uw @ xb) < 1e-12     # tangential
+            assert xb[0] * uw[1] - xb[1] * uw[0] > 0  # counter-clockwise
+        else:
+            assert not uw.any()
+
+
+def test_pipe_fractions_by_bisection():
+    w = W.tilted_pipe_3d(32)
+    a, R = w["axis"], w["radius"]
+    E = W.DIRECTIONS["D3Q19"].astype(float)
+    c0 = np.array([16, 16 + 0.37, 16 + 0.21])
+    ims = [np.array([0, my * 32, mz * 32.0]) for my in (-1, 0, 1) for mz in (-1, 0, 1)]
+
+    def dist(p):
+        best = np.inf
+        for im in ims:
+            v = p - c0 - im
+            v = v - (v @ a) * a
+            best = min(best, np.linalg.norm(v))
+        return best
+    L = w["links"]
+    for k in range(0, len(L["node"]), 37):
+        n = L["node"][k]
+        p = np.array([n % 32, (n // 32) % 32, n // 1024], dtype=float)
+        q = _bisect(lambda x: dist(x) >= R, p, E[L["d"][k]])
+        assert abs(q - L["q"][k]) < 1e-10
+
+
+def test_links_complete_and_sorted():
+    w = W.tilted_pipe_3d(16)
+    node, d = W.cut_links("D3Q19", w["shape"], w["skew"], w["solid"])
+    assert np.array_equal(node, w["links"]["node"]) and np.array_equal(d, w["links"]["d"])
+    assert np.all(np.diff(node) >= 0)
+    assert not w["solid"][node].any()
+    assert np.all((w["links"]["q"] > 0) & (w["links"]["q"] <= 1))
+
+
+def test_ensemble_is_seeded():
+    a = W.couette_ensemble(96, 0)
+    b = W.couette_ensemble(96, 0)
+    assert a == b
+    assert all(48 <= p["n"] <= 768 for p in a)
+    assert all(0.1 * p["n"] <= p["R1"] <= 0.25 * p["n"] for p in a)
