@@ -1,0 +1,388 @@
+"""Throughput benchmark of the fused D3Q19 MRT sweep with the single-node curved-wall
+scheme (arXiv:1712.08288, Eqs. 2.10/2.13) on one GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Workload: body-force driven flow in a circular pipe of radius 0.4 L whose axis
+(16, 4, 3) is tilted off the lattice axes, L = 256 (16.8M nodes, 8.8M fluid), wall
+fractions from the exact cylinder, periodic along the axis through a skewed x-wrap,
+l = gamma, b = 1.  One step = one fused collide/stream/boundary sweep over the grid
+(one kernel launch).  The headline value is fluid-node updates per second (MLUPS)
+with FP32 deviation storage; FP64 storage is timed on the same workload beside it,
+and the accuracy of both against the analytic Hagen-Poiseuille profile is reported
+after an untimed run.  The populations (1.27 GB in FP32) exceed L2 (129 MB), so
+no flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle (the only reference implementation of
+this method: the paper ships no code) on the host cores, on a bounded sample of
+the same workload family.
+
+Under torchrun (N > 1) every rank runs the same workload on its own GPU (replicas,
+weak scaling; the method needs no exchange between independent problems) and the
+slowest rank's time is reported.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D3Q19 MRT+curved-BC MLUPS & % HBM roofline, FP32 vs FP64 at matched L2 err"
+WORKLOAD = ("D3Q19 MRT body-force Poiseuille flow in a tilted periodic pipe, L=256 "
+            "(16.8M nodes), R=0.4L, axis (16,4,3), skewed x-wrap, single-node scheme l=gamma b=1")
+SCHEME = (0.0, 1.0, 0.0, 1.0)
+BYTES = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}
+PROFILE = os.path.join(ROOT, "profiles", "sweep_d3q19_f32_pipe256.txt")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1712_08288_gb300", "csrc", f)
+                  for f in ("sweep.cuh", "common.cuh", "lattice.h", "lbm_internal.h")]
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the FP32 sweep from the committed ncu summary, or
+    None when the summary is absent or the kernel source changed since."""
+    if not os.path.exists(PROFILE):
+        return None
+    vals = {}
+    with open(PROFILE) as fh:
+        for line in fh:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != kernel_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        top = sorted(sm)[len(sm) // 4:]          # samples under load
+        return {"sm_mhz": statistics.median(top), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def build_sim(w, precision, torch, stream):
+    from paper_1712_08288_gb300 import binding as B
+    sim = B.from_workload(w, precision, SCHEME)
+    sim.set_stream(stream.cuda_stream)
+    return sim
+
+
+def time_steps(sim, torch, stream, steps, warmup, per_launch=True):
+    """Warm-up, then K single-sweep launches bracketed by events; returns
+    (total ms, list of per-launch ms)."""
+    sim.step(warmup)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)] if per_launch else []
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(steps):
+        if per_launch:
+            ev[k][0].record(stream)
+        sim.step(1)
+        if per_launch:
+            ev[k][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    total = t0.elapsed_time(t1)
+    launches = [a.elapsed_time(b) for a, b in ev]
+    return total, launches
+
+
+def run_gpu(args):
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    from paper_1712_08288_gb300 import workloads as W
+
+    L = args.L
+    w = W.tilted_pipe_3d(L)
+    n_fluid = int((~w["solid"]).sum())
+    Q = 19
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- FP32 deviation storage: the headline --------------------------------
+    sim = build_sim(w, "f32", torch, stream)
+    sim.init_equilibrium(None, np.nan_to_num(w["u_exact"]))
+    barrier()
+    with ClockSampler(local) as clk:
+        total_ms, launches = time_steps(sim, torch, stream, args.steps, args.warmup)
+        barrier()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    mlups = n_fluid * args.steps * world / (total_ms * 1e-3) / 1e6
+    launch_ms = float(np.mean(launches))
+    hbm, peak_kind = peaks()
+    alg_bytes = 2 * Q * BYTES["f32"] * n_fluid          # populations read + written
+    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+    traffic = profiled_traffic()
+    status32 = sim.error_norms(None, check=False)["status"]
+    del sim
+
+    # ---- FP64 storage on the same workload -----------------------------------
+    sim = build_sim(w, "f64", torch, stream)
+    sim.init_equilibrium(None, np.nan_to_num(w["u_exact"]))
+    k64 = max(10, args.steps // 8)
+    total64, launches64 = time_steps(sim, torch, stream, k64, min(args.warmup, 5))
+    mlups64 = n_fluid * k64 / (total64 * 1e-3) / 1e6
+    l64 = float(np.mean(launches64))
+    ach64 = 2 * Q * BYTES["f64"] * n_fluid / (l64 * 1e-3) / 1e9
+    del sim
+
+    # ---- e2e through the C-ABI with host buffers ------------------------------
+    sim = build_sim(w, "f32", torch, stream)
+    N = L ** 3
+    u0 = torch.from_numpy(np.ascontiguousarray(np.nan_to_num(w["u_exact"]))).pin_memory().numpy()
+    rho_h = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+    u_h = torch.empty((N, 3), dtype=torch.float64).pin_memory().numpy()
+    sim.step(2)
+    barrier()
+    e0 = time.perf_counter()
+    sim.init_equilibrium(None, u0)                 # H2D of the initial field
+    sim.step(args.steps)
+    sim._check(sim._lib.lbm_moments(sim.h, rho_h.ctypes.data_as(__import__("ctypes").c_void_p),
+                                    u_h.ctypes.data_as(__import__("ctypes").c_void_p)))   # D2H
+    e_ms = (time.perf_counter() - e0) * 1e3
+    e2e = {"value": n_fluid * args.steps * world / (e_ms * 1e-3) / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": u0.nbytes / args.steps,
+           "d2h_bytes_per_step": (rho_h.nbytes + u_h.nbytes) / args.steps,
+           "note": "one job: initial field H2D, K sweeps, rho and u D2H; bytes per sweep"}
+    del sim
+
+    # ---- accuracy: FP32 vs FP64 against the analytic profile (untimed) --------
+    acc = None
+    if args.accuracy_steps > 0 and rank == 0:
+        acc = {}
+        wa = W.tilted_pipe_3d(args.accuracy_L)
+        for prec in ("f32", "f64"):
+            s2 = build_sim(wa, prec, torch, stream)
+            s2.init_equilibrium(None, np.nan_to_num(wa["u_exact"]))
+            s2.step(args.accuracy_steps)
+            nrm = s2.error_norms(np.nan_to_num(wa["u_exact"]), check=False)
+            acc[prec] = {"E_r": nrm["l2_rel"], "linf": nrm["linf"]}
+            del s2
+        acc["L"] = args.accuracy_L
+        acc["steps"] = args.accuracy_steps
+        acc["matched"] = abs(acc["f32"]["E_r"] - acc["f64"]["E_r"]) <= 0.1 * acc["f64"]["E_r"]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_L, args.cpu_steps)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("L=256", "L=%d" % L), "lattice": "D3Q19",
+                       "L": L, "nodes": N, "fluid_nodes": n_fluid, "links": len(w["links"]["node"]),
+                       "storage": "f32 deviations (f - w rho0), f32 arithmetic",
+                       "l2_policy": "inputs larger than L2 (%.2f GB populations)" % (Q * 4 * N / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
+                         "traffic": traffic, "kernel": "sweep_kernel<D3Q19,float>",
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "launch_ms": launch_ms},
+            "fp64": {"value": round(mlups64, 1), "unit": "MLUPS", "steps": k64,
+                     "launch_ms": l64, "achieved_GBs": round(ach64, 1),
+                     "frac_of_hbm": round(ach64 / hbm, 4),
+                     "note": "FP64 storage and arithmetic, same workload"},
+            "accuracy": acc,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+            "status_f32": status32,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _oracle_rate(L, steps, warmup):
+    """Run the oracle in a fresh single-threaded process; returns (MLUPS, seconds)."""
+    code = r"""
+import os, sys, time, json
+sys.path.insert(0, %r)
+import numpy as np
+from oracle import lattices as OL, lbm as O
+from paper_1712_08288_gb300 import workloads as W
+w = W.tilted_pipe_3d(%d)
+sim = O.Simulation(OL.D3Q19, w['shape'], w['S'], 1.0, w['solid'], w['links'], scheme=%r,
+                   force=w['force'], skew=w['skew'])
+sim.init_equilibrium(None, np.nan_to_num(w['u_exact']))
+sim.step(%d)
+t = time.perf_counter(); sim.step(%d); dt = time.perf_counter() - t
+nf = int((~w['solid']).sum())
+print(json.dumps({'mlups': nf * %d / dt / 1e6, 'seconds': dt, 'fluid': nf}))
+""" % (ROOT, L, SCHEME, warmup, steps, steps)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(L, steps):
+    res = _oracle_rate(L, steps, 1)
+    return {"value": round(res["mlups"], 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "FP64 numpy oracle, same pipe recipe at L=%d (%d fluid nodes), %d steps, "
+                      "%.1f s, single thread" % (L, res["fluid"], steps, res["seconds"])}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    # a sample size whose (steps + warmup) oracle steps end within ~2 minutes
+    per_node_s = 0.8e-6
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    L = 16
+    for cand in (64, 48, 32, 16):
+        if cand ** 3 * per_node_s <= budget:
+            L = cand
+            break
+    res = _oracle_rate(L, args.steps, args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": round(res["mlups"], 4), "unit": "MLUPS",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["seconds"] * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("L=256", "L=%d" % args.L), "lattice": "D3Q19",
+                       "L": args.L},
+            "cpu_baseline": {"value": round(res["mlups"], 4), "unit": "MLUPS", "cores": 1,
+                             "kind": "oracle",
+                             "sample": "each step: one oracle step of the same pipe recipe at "
+                                       "L=%d (%d fluid nodes), single thread" % (L, res["fluid"])},
+            "e2e": {"value": round(res["mlups"], 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--L", type=int, default=256)
+    ap.add_argument("--accuracy-L", type=int, default=128)
+    ap.add_argument("--accuracy-steps", type=int, default=20000)
+    ap.add_argument("--cpu-L", type=int, default=48)
+    ap.add_argument("--cpu-steps", type=int, default=60)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

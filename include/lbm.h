@@ -1,0 +1,178 @@
+/*
+ * lbm.h -- C-ABI of the GB300 lattice-Boltzmann library with the single-node
+ * second-order boundary schemes of Zhao & Yong, "A family of single-node
+ * second-order boundary schemes for the lattice Boltzmann method"
+ * (arXiv:1712.08288).
+ *
+ * What one step computes (lbm_step):
+ *   - collision, point-wise, MRT form  f' = f - M^-1 S M (f - f^eq)   (Eq. 2.2a;
+ *     Appendix), incompressible equilibrium of Eq. 42 with rho0 u = sum c_i f_i;
+ *   - body force: rho0*g added to the momentum moments after relaxation
+ *     (the paper uses a force, Sec. 3, but states no forcing scheme; this is the
+ *     library's reading, and the velocity it reports is u = j/rho0 + g/2);
+ *   - advection f_i(x + e_i, t+1) = f'_i(x, t) between fluid nodes (Eq. 2.2b);
+ *   - for every cut link the single-node boundary value (Eqs. 2.10 and 2.13):
+ *       f_i(x_f,t+1) = (1-b) f_i(x_f,t) + b [ (1+l-2g)/(1+l) f_ib(x_f,t)
+ *                      + l/(1+l) f'_i(x_f,t) + (2g-l)/(1+l) f'_ib(x_f,t)
+ *                      + 2/(1+l) w_i rho0 (e_i . phi(x_b)) / c_s^2 ]
+ *     with g = gamma = the link's wall fraction, ib the opposite of i, and
+ *     l = c0 + c1 g + c2 g^2 (the family parameter of Sec. 2; the five rules of
+ *     Sec. 3 are (0,1,0), (0,1.5,0), (0,2,0), (0,0,1), (0,1,1)).
+ *   Lattice units: h = delta_t = c = 1, c_s^2 = 1/3.
+ *
+ * Lattices and numbering:
+ *   LBM_D2Q9  directions 0..8 in the paper's Appendix order
+ *             (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1);
+ *             moments (rows of M, the Appendix matrix): rho, e, eps, j_x, q_x,
+ *             j_y, q_y, p_xx, p_xy.
+ *   LBM_D3Q19 (not in the paper; the 3D MRT family it cites, d'Humieres et al.
+ *             2002) directions 0..18: rest; +x,-x,+y,-y,+z,-z; (1,1,0),(-1,-1,0),
+ *             (1,-1,0),(-1,1,0), (1,0,1),(-1,0,-1),(1,0,-1),(-1,0,1), (0,1,1),
+ *             (0,-1,-1),(0,1,-1),(0,-1,1); moments rho, e, eps, j_x, q_x, j_y,
+ *             q_y, j_z, q_z, 3p_xx, 3pi_xx, p_ww, pi_ww, p_xy, p_yz, p_xz, m_x,
+ *             m_y, m_z.
+ *
+ * Grid: nx*ny*nz nodes (nz = 1 for D2Q9), node index n = x + nx*(y + ny*z).
+ *   Every axis is periodic; the x-wrap may be skewed (lbm_set_skew).  Walls that
+ *   are not periodic are expressed with solid nodes: a fluid node's every
+ *   neighbour is either fluid or a solid node with a cut link toward it.
+ *
+ * Conventions for every call:
+ *   - Host pointers are borrowed for the duration of the call and copied; the
+ *     caller keeps ownership.  "_device" calls take device pointers that the
+ *     caller owns (e.g. from PyTorch); the library never frees them.
+ *   - Every call returns an lbm_status and records a message readable with
+ *     lbm_last_error().  Nothing throws across the ABI.
+ *   - A context is not thread-safe.  Work is issued on the context's stream
+ *     (lbm_set_stream; default: the legacy default stream).  Calls that return
+ *     host data synchronise that stream.
+ *   - Device memory (populations, geometry) is allocated by the library with
+ *     cudaMalloc on the device current at lbm_create, and freed by lbm_destroy.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+enum lbm_lattice { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
+
+/* Storage precision of the populations.  F64 stores and computes in double.
+ * The _DEV variants store deviations g_i = f_i - w_i rho0 (the scheme is exact in
+ * that form: its coefficients sum to one and the equilibrium is linear in rho) and
+ * compute in float. */
+enum lbm_precision { LBM_F64 = 0, LBM_F32_DEV = 1, LBM_BF16_DEV = 2, LBM_F16_DEV = 3 };
+
+enum lbm_status {
+  LBM_OK = 0,
+  LBM_EINVAL = -1,      /* bad argument (message says which)                      */
+  LBM_ENOMEM = -2,      /* device or host allocation failed                       */
+  LBM_ECUDA = -3,       /* a CUDA call failed (message carries cudaGetErrorString) */
+  LBM_ENONCONVEX = -4,  /* a link's l violates Eq. 2.12 and nonconvex not allowed  */
+  LBM_EDIVERGED = -5,   /* a non-finite or runaway density was seen               */
+  LBM_ETIMEOUT = -6,    /* a bounded device wait gave up                          */
+  LBM_ESTATE = -7       /* call out of order (e.g. lbm_step before lbm_set_geometry) */
+};
+
+/* Create a context on the current CUDA device.
+ *   lattice   LBM_D2Q9 or LBM_D3Q19; nz must be 1 for D2Q9.
+ *   nx,ny,nz  grid size, each >= 1 (>= 3 along any axis a fluid link crosses).
+ *   s         Q relaxation rates in the moment order above (diagonal of S,
+ *             Appendix); the rates of rho and j have no effect (conserved).
+ *   precision an lbm_precision.
+ *   rho0      the mean density rho0 of Eq. 42 (> 0).
+ * Populations start at rest (f = w_i rho0); the geometry starts all-fluid; the
+ * scheme starts at l = gamma, b = 1 (Remark 4's special case); no force. */
+int lbm_create(lbm_ctx **out, int lattice, int nx, int ny, int nz,
+               const double *s, int precision, double rho0);
+int lbm_destroy(lbm_ctx *ctx);
+
+/* Stream on which all later work is issued (a cudaStream_t; NULL = legacy). */
+int lbm_set_stream(lbm_ctx *ctx, void *cuda_stream);
+
+/* Skewed x-periodicity: the field is invariant under the translation
+ * (nx, sy, sz); 0 <= sy < ny, 0 <= sz < nz.  Invalidates the geometry (call
+ * lbm_set_geometry again). */
+int lbm_set_skew(lbm_ctx *ctx, int sy, int sz);
+
+/* Geometry and cut links (Sec. 2, Fig. 1).
+ *   solid    nodes bytes, nonzero = solid (outside the fluid).
+ *   n_links  number of cut links.
+ *   node[k]  fluid node x_f of link k.
+ *   dir[k]   direction d pointing from x_f toward the wall: x_f + e_d is solid.
+ *            The population the scheme computes is i = opposite(d).
+ *   q[k]     wall fraction gamma in (0, 1]: the wall point is x_b = x_f + q e_d
+ *            (the paper's x_b = x_f - gamma h e_i).
+ *   uw       NULL (walls at rest) or 3*n_links wall velocities phi(x_b) (third
+ *            component ignored in 2D), held fixed in time.
+ * Every fluid->solid pair must be listed exactly once; anything else is
+ * LBM_EINVAL.  If the current scheme makes a link non-convex (Eq. 2.12) and
+ * non-convex schemes were not allowed, LBM_ENONCONVEX.  Resets the populations
+ * to rest. */
+int lbm_set_geometry(lbm_ctx *ctx, const uint8_t *solid, int64_t n_links,
+                     const int64_t *node, const int32_t *dir, const double *q,
+                     const double *uw);
+
+/* Family parameters (Sec. 2): l = c0 + c1*gamma + c2*gamma^2 (must be >= 0 for
+ * every gamma in (0,1]), b in (0, 1] (Eq. 2.13).  Unless allow_nonconvex, every
+ * link of the current geometry must satisfy max(0, 2g-1) <= l <= 2g (Eq. 2.12),
+ * else LBM_ENONCONVEX and the previous scheme stays. */
+int lbm_set_scheme(lbm_ctx *ctx, double c0, double c1, double c2, double b,
+                   int allow_nonconvex);
+
+/* Uniform body force g (lattice units, 3 components; g[2] ignored in 2D). */
+int lbm_set_force(lbm_ctx *ctx, const double g[3]);
+
+/* f = f^eq(rho, u) (Eq. 42) on fluid nodes.  rho: nodes doubles or NULL (rho0);
+ * u: D*nodes doubles (D = 2 or 3, node-major) or NULL (rest).  Time resets to 0. */
+int lbm_init_equilibrium(lbm_ctx *ctx, const double *rho, const double *u);
+
+/* Full populations f_i(x, t) (not deviations), Q*nodes doubles, f[i*nodes + n].
+ * set: values on solid nodes are ignored; time resets to 0.
+ * get: NaN on solid nodes; valid after any number of steps. */
+int lbm_set_populations(lbm_ctx *ctx, const double *f);
+int lbm_get_populations(lbm_ctx *ctx, double *f);
+
+/* Advance n >= 0 time steps (one fused collide-stream-boundary sweep each). */
+int lbm_step(lbm_ctx *ctx, int n);
+/* Number of steps taken since the last (re)initialisation. */
+int64_t lbm_time(const lbm_ctx *ctx);
+
+/* Density and reported velocity u = j/rho0 + g/2 (FP64) on fluid nodes, NaN on
+ * solid nodes.  rho: nodes doubles or NULL; u: D*nodes doubles or NULL. */
+int lbm_moments(lbm_ctx *ctx, double *rho, double *u);
+/* Same into caller-owned device buffers (no synchronisation). */
+int lbm_moments_device(lbm_ctx *ctx, double *rho_dev, double *u_dev);
+
+/* Error norms over fluid nodes, reduced on the GPU in FP64 (Sec. 3.1, E_r):
+ *   l2_rel  sqrt(sum |u_ref - u|^2) / sqrt(sum |u_ref|^2)   (u = LB velocity)
+ *   linf    max |u_ref - u| (component-wise maximum)
+ *   mass    sum of rho;  mom = sum of j = rho0 (u - g/2)
+ *   residual sqrt(sum |u - u_prev|^2)/sqrt(sum |u|^2), u_prev = the velocity at
+ *            the previous lbm_error_norms call (0 on the first call).
+ * u_ref: D*nodes doubles (host), or NULL to skip l2_rel/linf (set to NaN).
+ * Returns LBM_EDIVERGED (with the norms filled) if any density is non-finite. */
+typedef struct {
+  double l2_rel, linf, mass, mom[3], residual;
+} lbm_norms;
+int lbm_error_norms(lbm_ctx *ctx, const double *u_ref, lbm_norms *out);
+
+/* Sizes: lattice Q and D, node counts, link count. */
+int lbm_query(const lbm_ctx *ctx, int *Q, int *D, int64_t *nodes, int64_t *fluid_nodes,
+              int64_t *links);
+
+/* Message of the last failing call on ctx (or of the last failed lbm_create when
+ * ctx is NULL).  Never NULL. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,207 @@
+"""Thin ctypes binding of liblbm.so (include/lbm.h).  Argument marshalling only:
+every step of the computation runs in the library's CUDA kernels.
+
+The library must have been built (``python -m paper_1712_08288_gb300._build`` or
+``__graft_entry__.build()``); importing this module without it raises ImportError
+-- there is no CPU fallback.
+"""
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+
+LBM_D2Q9, LBM_D3Q19 = 0, 1
+LBM_F64, LBM_F32_DEV, LBM_BF16_DEV, LBM_F16_DEV = 0, 1, 2, 3
+PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32_DEV, "bf16": LBM_BF16_DEV, "f16": LBM_F16_DEV}
+LATTICES = {"D2Q9": LBM_D2Q9, "D3Q19": LBM_D3Q19}
+STATUS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA",
+          -4: "LBM_ENONCONVEX", -5: "LBM_EDIVERGED", -6: "LBM_ETIMEOUT", -7: "LBM_ESTATE"}
+
+# every symbol include/lbm.h declares
+EXPORTS = ["lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_set_skew", "lbm_set_geometry",
+           "lbm_set_scheme", "lbm_set_force", "lbm_init_equilibrium", "lbm_set_populations",
+           "lbm_get_populations", "lbm_step", "lbm_time", "lbm_moments", "lbm_moments_device",
+           "lbm_error_norms", "lbm_query", "lbm_last_error"]
+
+
+class lbm_norms(ct.Structure):
+    _fields_ = [("l2_rel", ct.c_double), ("linf", ct.c_double), ("mass", ct.c_double),
+                ("mom", ct.c_double * 3), ("residual", ct.c_double)]
+
+
+def load_library(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError("liblbm.so is not built (%s); run __graft_entry__.build()" % path)
+    lib = ct.CDLL(path)
+    P, D, I, I64 = ct.c_void_p, ct.c_double, ct.c_int, ct.c_int64
+    sig = {
+        "lbm_create": (I, [ct.POINTER(P), I, I, I, I, P, I, D]),
+        "lbm_destroy": (I, [P]),
+        "lbm_set_stream": (I, [P, P]),
+        "lbm_set_skew": (I, [P, I, I]),
+        "lbm_set_geometry": (I, [P, P, I64, P, P, P, P]),
+        "lbm_set_scheme": (I, [P, D, D, D, D, I]),
+        "lbm_set_force": (I, [P, P]),
+        "lbm_init_equilibrium": (I, [P, P, P]),
+        "lbm_set_populations": (I, [P, P]),
+        "lbm_get_populations": (I, [P, P]),
+        "lbm_step": (I, [P, I]),
+        "lbm_time": (I64, [P]),
+        "lbm_moments": (I, [P, P, P]),
+        "lbm_moments_device": (I, [P, P, P]),
+        "lbm_error_norms": (I, [P, P, ct.POINTER(lbm_norms)]),
+        "lbm_query": (I, [P, P, P, P, P, P]),
+        "lbm_last_error": (ct.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ct.c_void_p)
+
+
+class Lbm:
+    """One simulation context (lbm_ctx).  Method names follow the C-ABI."""
+
+    def __init__(self, lattice, shape, s, precision="f64", rho0=1.0):
+        self._lib = lib()
+        self.lattice = lattice
+        self.lat_id = LATTICES[lattice]
+        self.shape = tuple(int(v) for v in shape)
+        self.precision = precision
+        self.rho0 = float(rho0)
+        self.Q = 9 if lattice == "D2Q9" else 19
+        self.D = 2 if lattice == "D2Q9" else 3
+        self.N = self.shape[0] * self.shape[1] * self.shape[2]
+        s = np.ascontiguousarray(s, dtype=np.float64)
+        assert s.shape == (self.Q,)
+        h = ct.c_void_p()
+        rc = self._lib.lbm_create(ct.byref(h), self.lat_id, *self.shape, _ptr(s),
+                                  PRECISIONS[precision], self.rho0)
+        if rc != 0:
+            raise LbmError(rc, self._lib.lbm_last_error(None).decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc != 0:
+            raise LbmError(rc, self._lib.lbm_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- setup -------------------------------------------------------------
+    def set_stream(self, stream_handle):
+        self._check(self._lib.lbm_set_stream(self.h, ct.c_void_p(stream_handle)))
+
+    def set_skew(self, sy, sz):
+        self._check(self._lib.lbm_set_skew(self.h, int(sy), int(sz)))
+
+    def set_geometry(self, solid, links):
+        solid = np.ascontiguousarray(np.asarray(solid).reshape(self.N), dtype=np.uint8)
+        node = np.ascontiguousarray(links["node"], dtype=np.int64)
+        d = np.ascontiguousarray(links["d"], dtype=np.int32)
+        q = np.ascontiguousarray(links["q"], dtype=np.float64)
+        uw = links.get("uw")
+        uw = None if uw is None else np.ascontiguousarray(np.asarray(uw, dtype=np.float64).reshape(-1, 3))
+        self._check(self._lib.lbm_set_geometry(self.h, _ptr(solid), len(node), _ptr(node), _ptr(d),
+                                               _ptr(q), _ptr(uw)))
+
+    def set_scheme(self, c0, c1, c2, b=1.0, allow_nonconvex=False):
+        self._check(self._lib.lbm_set_scheme(self.h, c0, c1, c2, b, int(bool(allow_nonconvex))))
+
+    def set_force(self, g):
+        g = np.ascontiguousarray(list(g) + [0.0] * (3 - len(g)), dtype=np.float64)
+        self._check(self._lib.lbm_set_force(self.h, _ptr(g)))
+
+    def init_equilibrium(self, rho=None, u=None):
+        rho = None if rho is None else np.ascontiguousarray(np.asarray(rho).reshape(self.N), dtype=np.float64)
+        if u is not None:
+            u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(self.N, -1)[:, : self.D])
+        self._check(self._lib.lbm_init_equilibrium(self.h, _ptr(rho), _ptr(u)))
+
+    def set_populations(self, f):
+        f = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(self.Q, self.N))
+        self._check(self._lib.lbm_set_populations(self.h, _ptr(f)))
+
+    # -- run / read ----------------------------------------------------------
+    def step(self, n=1):
+        self._check(self._lib.lbm_step(self.h, int(n)))
+
+    def time(self):
+        return int(self._lib.lbm_time(self.h))
+
+    def get_populations(self):
+        f = np.empty((self.Q, self.N), dtype=np.float64)
+        self._check(self._lib.lbm_get_populations(self.h, _ptr(f)))
+        return f
+
+    def moments(self):
+        rho = np.empty(self.N, dtype=np.float64)
+        u = np.empty((self.N, self.D), dtype=np.float64)
+        self._check(self._lib.lbm_moments(self.h, _ptr(rho), _ptr(u)))
+        return rho, u
+
+    def moments_device(self, rho_ptr, u_ptr):
+        self._check(self._lib.lbm_moments_device(self.h, ct.c_void_p(rho_ptr), ct.c_void_p(u_ptr)))
+
+    def error_norms(self, u_ref=None, check=True):
+        out = lbm_norms()
+        if u_ref is not None:
+            u_ref = np.ascontiguousarray(np.asarray(u_ref, dtype=np.float64).reshape(self.N, -1)[:, : self.D])
+        rc = self._lib.lbm_error_norms(self.h, _ptr(u_ref), ct.byref(out))
+        if check:
+            self._check(rc)
+        return dict(l2_rel=out.l2_rel, linf=out.linf, mass=out.mass, mom=list(out.mom),
+                    residual=out.residual, status=rc)
+
+    def query(self):
+        Q, D = ct.c_int(), ct.c_int()
+        n, nf, nl = ct.c_int64(), ct.c_int64(), ct.c_int64()
+        self._check(self._lib.lbm_query(self.h, ct.byref(Q), ct.byref(D), ct.byref(n), ct.byref(nf),
+                                        ct.byref(nl)))
+        return dict(Q=Q.value, D=D.value, nodes=n.value, fluid_nodes=nf.value, links=nl.value)
+
+
+def from_workload(w, precision="f64", scheme=(0.0, 1.0, 0.0, 1.0), allow_nonconvex=False):
+    """Build a context from an input-generator dict (workloads module)."""
+    sim = Lbm(w["lattice"], w["shape"], w["S"], precision, w.get("rho0", 1.0))
+    if tuple(w.get("skew", (0, 0))) != (0, 0):
+        sim.set_skew(*w["skew"])
+    sim.set_scheme(*scheme, allow_nonconvex=True)   # geometry not yet set: no links to check
+    sim.set_geometry(w["solid"], w["links"])
+    sim.set_scheme(*scheme, allow_nonconvex=allow_nonconvex)
+    sim.set_force(w.get("force", (0.0, 0.0, 0.0)))
+    return sim

@@ -1,0 +1,610 @@
+// lbm_capi.cu -- the C-ABI of include/lbm.h: context, argument validation,
+// geometry compaction (cut links of Sec. 2 into per-node records and per-link
+// coefficients of Eq. 2.13), and the host side of every call.  All arithmetic of
+// a time step runs in the kernels (sweep_*.cu, aux_kernels.cu).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lattice.h"
+#include "lbm_internal.h"
+
+namespace lbm {
+cudaError_t launch_sweep_d2q9(int, bool, const SweepArgs<double> &, const SweepArgs<float> &,
+                              cudaStream_t);
+cudaError_t launch_sweep_d3q19(int, bool, const SweepArgs<double> &, const SweepArgs<float> &,
+                               cudaStream_t);
+cudaError_t launch_sweep(int lattice, int precision, bool odd, const SweepArgs<double> &a64,
+                         const SweepArgs<float> &a32, cudaStream_t st) {
+  return lattice == LBM_D2Q9 ? launch_sweep_d2q9(precision, odd, a64, a32, st)
+                             : launch_sweep_d3q19(precision, odd, a64, a32, st);
+}
+}  // namespace lbm
+
+using namespace lbm;
+
+struct lbm_ctx {
+  int lattice = 0, Q = 0, D = 0, precision = 0;
+  int nx = 0, ny = 0, nz = 0, sy = 0, sz = 0;
+  long long N = 0;
+  double rho0 = 1.0;
+  double s[19] = {0};
+  double c0 = 0.0, c1 = 1.0, c2 = 0.0, b = 1.0;
+  bool allow_nonconvex = false;
+  double g[3] = {0, 0, 0};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  long long t = 0;
+  bool geometry_set = false;
+
+  // device buffers
+  void *pop = nullptr;
+  uint8_t *cls = nullptr;
+  int32_t *bidx = nullptr;
+  uint32_t *bmask = nullptr;
+  int32_t *boff = nullptr;
+  void *coef = nullptr;
+  int *status = nullptr;
+  double *partials = nullptr;   // norm reduction scratch
+  double *norm_out = nullptr;
+  double *u_ref = nullptr;
+  double *u_prev = nullptr;
+  double *mom_rho = nullptr;
+  double *mom_u = nullptr;
+
+  // host copy of the cut links in device order (for re-deriving coefficients)
+  std::vector<int32_t> link_dir;
+  std::vector<double> link_q;
+  std::vector<double> link_uw;  // 3 per link
+  long long n_links = 0, n_fluid = 0, n_boundary = 0;
+
+  SweepArgs<double> a64;
+  SweepArgs<float> a32;
+  std::string err;
+};
+
+static std::string g_create_error = "no error";
+
+static int fail(lbm_ctx *c, int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  else g_create_error = buf;
+  return code;
+}
+
+#define CUDA_OR_FAIL(ctx, call)                                                      \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA,     \
+                  "%s: %s", #call, cudaGetErrorString(e_));                          \
+  } while (0)
+
+static int store_bytes(int precision) {
+  return precision == LBM_F64 ? 8 : (precision == LBM_F32_DEV ? 4 : 2);
+}
+
+template <class F>
+static auto with_lat(int lattice, F &&f) {
+  return lattice == LBM_D2Q9 ? f(D2Q9{}) : f(D3Q19{});
+}
+
+static long long wrap_host(const lbm_ctx *c, int x, int y, int z, int dx, int dy, int dz) {
+  int xs = x + dx, ys = y + dy, zs = z + dz;
+  if (xs < 0) { xs += c->nx; ys += c->sy; zs += c->sz; }
+  else if (xs >= c->nx) { xs -= c->nx; ys -= c->sy; zs -= c->sz; }
+  if (ys < 0) ys += c->ny; else if (ys >= c->ny) ys -= c->ny;
+  if (zs < 0) zs += c->nz; else if (zs >= c->nz) zs -= c->nz;
+  return xs + (long long)c->nx * (ys + (long long)c->ny * zs);
+}
+
+static AuxArgs aux_args(const lbm_ctx *c) {
+  AuxArgs a;
+  a.pop = c->pop;
+  a.N = c->N;
+  a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.sy = c->sy; a.sz = c->sz;
+  a.cls = c->cls;
+  a.rho0 = c->rho0;
+  for (int k = 0; k < 3; ++k) a.g[k] = c->g[k];
+  return a;
+}
+
+static void refresh_args(lbm_ctx *c) {
+  DevGeometry geo;
+  geo.cls = c->cls; geo.bidx = c->bidx; geo.bmask = c->bmask; geo.boff = c->boff;
+  geo.coef = c->coef;
+  auto fill = [&](auto &a) {
+    using C = std::remove_reference_t<decltype(a.inv_rho0)>;
+    a.pop = c->pop;
+    a.N = c->N;
+    a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.sy = c->sy; a.sz = c->sz;
+    a.geo = geo;
+    with_lat(c->lattice, [&](auto lat) {
+      using L = decltype(lat);
+      for (int k = 0; k < 19; ++k) a.sn[k] = C(0);
+      for (int k = 0; k < L::Q; ++k)
+        if (!L::conserved(k)) a.sn[k] = C(c->s[k] / row_norm2<L>(k));
+      for (int k = 0; k < 3; ++k) a.F[k] = C(c->rho0 * c->g[k] / L::kNormJ);
+      if (L::D == 2) a.F[2] = C(0);
+      return 0;
+    });
+    a.inv_rho0 = C(1.0 / c->rho0);
+    a.one_minus_b = C(1.0 - c->b);
+    a.status = c->status;
+  };
+  fill(c->a64);
+  fill(c->a32);
+}
+
+// l(gamma) of the family (Sec. 2 / Sec. 3 rules)
+static double l_of(const lbm_ctx *c, double q) { return c->c0 + c->c1 * q + c->c2 * q * q; }
+
+// Eq. 2.12
+static bool convex(double q, double l) {
+  return l >= std::max(0.0, 2.0 * q - 1.0) && l <= 2.0 * q;
+}
+
+// coefficients of Eq. 2.13 (b folded in) for every link, uploaded in the
+// compute type of the storage precision
+static int upload_coefficients(lbm_ctx *c) {
+  const long long nl = c->n_links;
+  if (nl == 0) return LBM_OK;
+  std::vector<double> co(4 * nl);
+  with_lat(c->lattice, [&](auto lat) {
+    using L = decltype(lat);
+    for (long long k = 0; k < nl; ++k) {
+      const int d = c->link_dir[k];
+      const int i = L::opp(d);
+      const double q = c->link_q[k];
+      const double l = l_of(c, q);
+      const double inv = 1.0 / (1.0 + l);
+      const double A = (1.0 + l - 2.0 * q) * inv;       // on f_ib(x_f, t), ib = d
+      const double B = l * inv;                         // on f'_i(x_f, t)
+      const double Cc = (2.0 * q - l) * inv;            // on f'_ib(x_f, t)
+      const double edotphi = L::ex(i) * c->link_uw[3 * k] + L::ey(i) * c->link_uw[3 * k + 1] +
+                             L::ez(i) * c->link_uw[3 * k + 2];
+      // 2/(1+l) w_i rho0 e_i.phi / c_s^2 with c_s^2 = 1/3
+      const double W = 2.0 * inv * L::w(i) * c->rho0 * edotphi * 3.0;
+      co[4 * k + 0] = c->b * A;
+      co[4 * k + 1] = c->b * B;
+      co[4 * k + 2] = c->b * Cc;
+      co[4 * k + 3] = c->b * W;
+    }
+    return 0;
+  });
+  if (c->precision == LBM_F64) {
+    CUDA_OR_FAIL(c, cudaMemcpy(c->coef, co.data(), sizeof(double) * co.size(),
+                               cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> cf(co.begin(), co.end());
+    CUDA_OR_FAIL(c, cudaMemcpy(c->coef, cf.data(), sizeof(float) * cf.size(),
+                               cudaMemcpyHostToDevice));
+  }
+  return LBM_OK;
+}
+
+static void free_geometry(lbm_ctx *c) {
+  cudaFree(c->bidx); c->bidx = nullptr;
+  cudaFree(c->bmask); c->bmask = nullptr;
+  cudaFree(c->boff); c->boff = nullptr;
+  cudaFree(c->coef); c->coef = nullptr;
+}
+
+extern "C" {
+
+int lbm_create(lbm_ctx **out, int lattice, int nx, int ny, int nz, const double *s,
+               int precision, double rho0) {
+  if (!out) return fail(nullptr, LBM_EINVAL, "lbm_create: out is NULL");
+  *out = nullptr;
+  if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19)
+    return fail(nullptr, LBM_EINVAL, "lbm_create: unknown lattice %d", lattice);
+  if (precision < LBM_F64 || precision > LBM_F16_DEV)
+    return fail(nullptr, LBM_EINVAL, "lbm_create: unknown precision %d", precision);
+  if (nx < 1 || ny < 1 || nz < 1)
+    return fail(nullptr, LBM_EINVAL, "lbm_create: grid %dx%dx%d", nx, ny, nz);
+  if (lattice == LBM_D2Q9 && nz != 1)
+    return fail(nullptr, LBM_EINVAL, "lbm_create: D2Q9 needs nz == 1");
+  if (!s) return fail(nullptr, LBM_EINVAL, "lbm_create: s is NULL");
+  if (!(rho0 > 0) || !std::isfinite(rho0))
+    return fail(nullptr, LBM_EINVAL, "lbm_create: rho0 must be > 0");
+  const int Q = lattice == LBM_D2Q9 ? 9 : 19;
+  for (int k = 0; k < Q; ++k)
+    if (!std::isfinite(s[k]) || s[k] < 0 || s[k] > 2)
+      return fail(nullptr, LBM_EINVAL, "lbm_create: s[%d] = %g outside [0, 2]", k, s[k]);
+  const long long N = (long long)nx * ny * nz;
+  if (N > (1LL << 31) - 1) return fail(nullptr, LBM_EINVAL, "lbm_create: more than 2^31 nodes");
+
+  lbm_ctx *c = new (std::nothrow) lbm_ctx();
+  if (!c) return fail(nullptr, LBM_ENOMEM, "lbm_create: host allocation");
+  c->lattice = lattice; c->Q = Q; c->D = lattice == LBM_D2Q9 ? 2 : 3;
+  c->precision = precision;
+  c->nx = nx; c->ny = ny; c->nz = nz; c->N = N;
+  c->rho0 = rho0;
+  for (int k = 0; k < Q; ++k) c->s[k] = s[k];
+  cudaError_t e = cudaGetDevice(&c->device);
+  size_t pop_bytes = (size_t)Q * N * store_bytes(precision);
+  if (e == cudaSuccess) e = cudaMalloc(&c->pop, pop_bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->cls, N);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->pop, 0, pop_bytes);
+  if (e == cudaSuccess) e = cudaMemset(c->cls, kFluid, N);
+  if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    int code = e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+    fail(nullptr, code, "lbm_create: %s", cudaGetErrorString(e));
+    lbm_destroy(c);
+    return code;
+  }
+  c->n_fluid = N;
+  c->geometry_set = true;  // all-fluid periodic box, no links
+  refresh_args(c);
+  *out = c;
+  return LBM_OK;
+}
+
+int lbm_destroy(lbm_ctx *c) {
+  if (!c) return LBM_OK;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  cudaFree(c->pop);
+  cudaFree(c->cls);
+  cudaFree(c->status);
+  free_geometry(c);
+  cudaFree(c->partials);
+  cudaFree(c->norm_out);
+  cudaFree(c->u_ref);
+  cudaFree(c->u_prev);
+  cudaFree(c->mom_rho);
+  cudaFree(c->mom_u);
+  delete c;
+  return LBM_OK;
+}
+
+int lbm_set_stream(lbm_ctx *c, void *stream) {
+  if (!c) return LBM_EINVAL;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return LBM_OK;
+}
+
+int lbm_set_skew(lbm_ctx *c, int sy, int sz) {
+  if (!c) return LBM_EINVAL;
+  if (sy < 0 || sy >= c->ny || sz < 0 || sz >= c->nz)
+    return fail(c, LBM_EINVAL, "lbm_set_skew: need 0 <= sy < ny and 0 <= sz < nz");
+  c->sy = sy;
+  c->sz = sz;
+  c->geometry_set = false;
+  refresh_args(c);
+  return LBM_OK;
+}
+
+int lbm_set_geometry(lbm_ctx *c, const uint8_t *solid, int64_t n_links, const int64_t *node,
+                     const int32_t *dir, const double *q, const double *uw) {
+  if (!c) return LBM_EINVAL;
+  if (!solid) return fail(c, LBM_EINVAL, "lbm_set_geometry: solid is NULL");
+  if (n_links < 0 || (n_links > 0 && (!node || !dir || !q)))
+    return fail(c, LBM_EINVAL, "lbm_set_geometry: bad link arrays");
+  cudaSetDevice(c->device);
+  const long long N = c->N;
+  const int Q = c->Q;
+  int rc = LBM_OK;
+  std::vector<uint32_t> mask(N, 0);
+  // every listed link: fluid node, solid neighbour, gamma in (0,1], no duplicate
+  for (long long k = 0; k < n_links; ++k) {
+    const long long n = node[k];
+    const int d = dir[k];
+    if (n < 0 || n >= N) return fail(c, LBM_EINVAL, "link %lld: node %lld out of range", k, n);
+    if (d < 1 || d >= Q) return fail(c, LBM_EINVAL, "link %lld: direction %d out of range", k, d);
+    if (solid[n]) return fail(c, LBM_EINVAL, "link %lld: node %lld is solid", k, n);
+    if (!(q[k] > 0.0 && q[k] <= 1.0))
+      return fail(c, LBM_EINVAL, "link %lld: wall fraction %g not in (0, 1]", k, q[k]);
+    if (uw && !(std::isfinite(uw[3 * k]) && std::isfinite(uw[3 * k + 1]) &&
+                std::isfinite(uw[3 * k + 2])))
+      return fail(c, LBM_EINVAL, "link %lld: non-finite wall velocity", k);
+    const int x = (int)(n % c->nx), y = (int)((n / c->nx) % c->ny), z = (int)(n / ((long long)c->nx * c->ny));
+    long long nb = with_lat(c->lattice, [&](auto lat) {
+      using L = decltype(lat);
+      return wrap_host(c, x, y, z, L::ex(d), L::ey(d), L::ez(d));
+    });
+    if (!solid[nb])
+      return fail(c, LBM_EINVAL, "link %lld: neighbour of node %lld along %d is fluid", k, n, d);
+    if (mask[n] & (1u << d)) return fail(c, LBM_EINVAL, "link %lld: duplicate (%lld, %d)", k, n, d);
+    mask[n] |= 1u << d;
+  }
+  // completeness: every fluid -> solid pair is listed (parallel over z-slabs)
+  {
+    const int nt = std::max(1, std::min<int>(std::thread::hardware_concurrency(), 32));
+    std::vector<long long> bad(nt, -1);
+    std::vector<std::thread> th;
+    for (int w = 0; w < nt; ++w)
+      th.emplace_back([&, w] {
+        with_lat(c->lattice, [&](auto lat) {
+          using L = decltype(lat);
+          for (long long n = w; n < N; n += nt) {
+            if (solid[n]) continue;
+            const int x = (int)(n % c->nx), y = (int)((n / c->nx) % c->ny),
+                      z = (int)(n / ((long long)c->nx * c->ny));
+            for (int d = 1; d < L::Q; ++d) {
+              const long long nb = wrap_host(c, x, y, z, L::ex(d), L::ey(d), L::ez(d));
+              if (solid[nb] && !(mask[n] & (1u << d))) {
+                bad[w] = n * 32 + d;
+                return 0;
+              }
+            }
+          }
+          return 0;
+        });
+      });
+    for (auto &t : th) t.join();
+    for (long long v : bad)
+      if (v >= 0)
+        return fail(c, LBM_EINVAL, "no cut link listed for node %lld direction %lld (solid neighbour)",
+                    v / 32, v % 32);
+  }
+  // convexity of the current scheme on every link (Eq. 2.12)
+  for (long long k = 0; k < n_links; ++k) {
+    const double l = l_of(c, q[k]);
+    if (l < 0) return fail(c, LBM_EINVAL, "link %lld: l = %g < 0", k, l);
+    if (!c->allow_nonconvex && !convex(q[k], l))
+      return fail(c, LBM_ENONCONVEX, "link %lld: l = %g violates Eq. 2.12 at gamma = %g", k, l, q[k]);
+  }
+  // compaction: boundary records in node order, links in (node, d) order
+  std::vector<uint8_t> cls(N);
+  std::vector<int32_t> bidx(N, -1);
+  std::vector<uint32_t> bmask;
+  std::vector<int32_t> boff;
+  long long nf = 0, off = 0;
+  for (long long n = 0; n < N; ++n) {
+    if (solid[n]) { cls[n] = kSolid; continue; }
+    ++nf;
+    if (mask[n]) {
+      cls[n] = kBoundary;
+      bidx[n] = (int32_t)bmask.size();
+      bmask.push_back(mask[n]);
+      boff.push_back((int32_t)off);
+      off += __builtin_popcount(mask[n]);
+    } else {
+      cls[n] = kFluid;
+    }
+  }
+  c->link_dir.assign(n_links, 0);
+  c->link_q.assign(n_links, 0.0);
+  c->link_uw.assign(3 * n_links, 0.0);
+  for (long long k = 0; k < n_links; ++k) {
+    const long long n = node[k];
+    const int d = dir[k];
+    const long long pos = boff[bidx[n]] + __builtin_popcount(mask[n] & ((1u << d) - 1u));
+    c->link_dir[pos] = d;
+    c->link_q[pos] = q[k];
+    if (uw)
+      for (int a = 0; a < 3; ++a) c->link_uw[3 * pos + a] = uw[3 * k + a];
+  }
+  // upload
+  free_geometry(c);
+  c->geometry_set = false;
+  c->n_links = n_links;
+  c->n_fluid = nf;
+  c->n_boundary = (long long)bmask.size();
+  const size_t cb = c->precision == LBM_F64 ? sizeof(double) : sizeof(float);
+  CUDA_OR_FAIL(c, cudaMemcpy(c->cls, cls.data(), N, cudaMemcpyHostToDevice));
+  CUDA_OR_FAIL(c, cudaMalloc((void **)&c->bidx, sizeof(int32_t) * N));
+  CUDA_OR_FAIL(c, cudaMemcpy(c->bidx, bidx.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice));
+  const size_t nb = std::max<size_t>(1, bmask.size());
+  CUDA_OR_FAIL(c, cudaMalloc((void **)&c->bmask, sizeof(uint32_t) * nb));
+  CUDA_OR_FAIL(c, cudaMalloc((void **)&c->boff, sizeof(int32_t) * nb));
+  CUDA_OR_FAIL(c, cudaMalloc(&c->coef, 4 * cb * std::max<long long>(1, n_links)));
+  if (!bmask.empty()) {
+    CUDA_OR_FAIL(c, cudaMemcpy(c->bmask, bmask.data(), sizeof(uint32_t) * bmask.size(),
+                               cudaMemcpyHostToDevice));
+    CUDA_OR_FAIL(c, cudaMemcpy(c->boff, boff.data(), sizeof(int32_t) * boff.size(),
+                               cudaMemcpyHostToDevice));
+  }
+  if ((rc = upload_coefficients(c)) != LBM_OK) return rc;
+  CUDA_OR_FAIL(c, cudaMemset(c->pop, 0, (size_t)c->Q * N * store_bytes(c->precision)));
+  CUDA_OR_FAIL(c, cudaMemset(c->status, 0, sizeof(int)));
+  cudaFree(c->u_prev);
+  c->u_prev = nullptr;
+  c->t = 0;
+  c->geometry_set = true;
+  refresh_args(c);
+  return LBM_OK;
+}
+
+int lbm_set_scheme(lbm_ctx *c, double c0, double c1, double c2, double b, int allow_nonconvex) {
+  if (!c) return LBM_EINVAL;
+  if (!(std::isfinite(c0) && std::isfinite(c1) && std::isfinite(c2)))
+    return fail(c, LBM_EINVAL, "lbm_set_scheme: non-finite l coefficients");
+  if (!(b > 0.0 && b <= 1.0)) return fail(c, LBM_EINVAL, "lbm_set_scheme: b = %g not in (0, 1]", b);
+  // l >= 0 on (0, 1]: check the ends and the vertex of the parabola
+  auto lq = [&](double q) { return c0 + c1 * q + c2 * q * q; };
+  double lmin = std::min(lq(1e-300), lq(1.0));
+  if (c2 != 0.0) {
+    const double v = -c1 / (2.0 * c2);
+    if (v > 0.0 && v < 1.0) lmin = std::min(lmin, lq(v));
+  }
+  if (lmin < 0.0) return fail(c, LBM_EINVAL, "lbm_set_scheme: l < 0 for some gamma in (0, 1]");
+  if (!allow_nonconvex)
+    for (long long k = 0; k < c->n_links; ++k) {
+      const double l = lq(c->link_q[k]);
+      if (!convex(c->link_q[k], l))
+        return fail(c, LBM_ENONCONVEX, "lbm_set_scheme: link %lld (gamma = %g) gets l = %g outside Eq. 2.12",
+                    k, c->link_q[k], l);
+    }
+  c->c0 = c0; c->c1 = c1; c->c2 = c2; c->b = b;
+  c->allow_nonconvex = allow_nonconvex != 0;
+  cudaSetDevice(c->device);
+  int rc = upload_coefficients(c);
+  refresh_args(c);
+  return rc;
+}
+
+int lbm_set_force(lbm_ctx *c, const double g[3]) {
+  if (!c || !g) return LBM_EINVAL;
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(g[k])) return fail(c, LBM_EINVAL, "lbm_set_force: non-finite force");
+  for (int k = 0; k < 3; ++k) c->g[k] = (k < c->D) ? g[k] : 0.0;
+  refresh_args(c);
+  return LBM_OK;
+}
+
+int lbm_init_equilibrium(lbm_ctx *c, const double *rho, const double *u) {
+  if (!c) return LBM_EINVAL;
+  if (!c->geometry_set) return fail(c, LBM_ESTATE, "lbm_init_equilibrium: geometry not set");
+  cudaSetDevice(c->device);
+  // staging buffers are the context's moment buffers (same sizes), kept for reuse
+  if (rho) {
+    if (!c->mom_rho) CUDA_OR_FAIL(c, cudaMalloc(&c->mom_rho, sizeof(double) * c->N));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->mom_rho, rho, sizeof(double) * c->N, cudaMemcpyHostToDevice,
+                                    c->stream));
+  }
+  if (u) {
+    if (!c->mom_u) CUDA_OR_FAIL(c, cudaMalloc(&c->mom_u, sizeof(double) * c->N * c->D));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->mom_u, u, sizeof(double) * c->N * c->D,
+                                    cudaMemcpyHostToDevice, c->stream));
+  }
+  CUDA_OR_FAIL(c, launch_init_equilibrium(c->lattice, c->precision, aux_args(c),
+                                          rho ? c->mom_rho : nullptr, u ? c->mom_u : nullptr,
+                                          c->stream));
+  CUDA_OR_FAIL(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+  CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+  c->t = 0;
+  return LBM_OK;
+}
+
+int lbm_set_populations(lbm_ctx *c, const double *f) {
+  if (!c || !f) return LBM_EINVAL;
+  if (!c->geometry_set) return fail(c, LBM_ESTATE, "lbm_set_populations: geometry not set");
+  cudaSetDevice(c->device);
+  double *df = nullptr;
+  const size_t bytes = sizeof(double) * c->Q * c->N;
+  CUDA_OR_FAIL(c, cudaMalloc(&df, bytes));
+  CUDA_OR_FAIL(c, cudaMemcpyAsync(df, f, bytes, cudaMemcpyHostToDevice, c->stream));
+  CUDA_OR_FAIL(c, launch_set_populations(c->lattice, c->precision, aux_args(c), df, c->stream));
+  CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+  cudaFree(df);
+  CUDA_OR_FAIL(c, cudaMemset(c->status, 0, sizeof(int)));
+  c->t = 0;
+  return LBM_OK;
+}
+
+int lbm_get_populations(lbm_ctx *c, double *f) {
+  if (!c || !f) return LBM_EINVAL;
+  cudaSetDevice(c->device);
+  double *df = nullptr;
+  const size_t bytes = sizeof(double) * c->Q * c->N;
+  CUDA_OR_FAIL(c, cudaMalloc(&df, bytes));
+  CUDA_OR_FAIL(c, launch_get_populations(c->lattice, c->precision, aux_args(c), (c->t & 1) != 0,
+                                         df, c->stream));
+  CUDA_OR_FAIL(c, cudaMemcpyAsync(f, df, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+  cudaFree(df);
+  return LBM_OK;
+}
+
+int lbm_step(lbm_ctx *c, int n) {
+  if (!c) return LBM_EINVAL;
+  if (n < 0) return fail(c, LBM_EINVAL, "lbm_step: n = %d < 0", n);
+  if (!c->geometry_set) return fail(c, LBM_ESTATE, "lbm_step: geometry not set");
+  for (int k = 0; k < n; ++k) {
+    const cudaError_t e = launch_sweep(c->lattice, c->precision, (c->t & 1) != 0, c->a64, c->a32,
+                                       c->stream);
+    if (e != cudaSuccess) return fail(c, LBM_ECUDA, "lbm_step: %s", cudaGetErrorString(e));
+    ++c->t;
+  }
+  return LBM_OK;
+}
+
+int64_t lbm_time(const lbm_ctx *c) { return c ? c->t : -1; }
+
+static int check_status(lbm_ctx *c) {
+  int h = 0;
+  CUDA_OR_FAIL(c, cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+  if (h) return fail(c, LBM_EDIVERGED, "a non-finite or runaway density was seen");
+  return LBM_OK;
+}
+
+int lbm_moments_device(lbm_ctx *c, double *rho_dev, double *u_dev) {
+  if (!c) return LBM_EINVAL;
+  cudaSetDevice(c->device);
+  CUDA_OR_FAIL(c, launch_moments(c->lattice, c->precision, aux_args(c), (c->t & 1) != 0, rho_dev,
+                                 u_dev, c->stream));
+  return LBM_OK;
+}
+
+int lbm_moments(lbm_ctx *c, double *rho, double *u) {
+  if (!c) return LBM_EINVAL;
+  cudaSetDevice(c->device);
+  if (rho && !c->mom_rho) CUDA_OR_FAIL(c, cudaMalloc(&c->mom_rho, sizeof(double) * c->N));
+  if (u && !c->mom_u) CUDA_OR_FAIL(c, cudaMalloc(&c->mom_u, sizeof(double) * c->N * c->D));
+  int rc = lbm_moments_device(c, rho ? c->mom_rho : nullptr, u ? c->mom_u : nullptr);
+  if (rc != LBM_OK) return rc;
+  if (rho)
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(rho, c->mom_rho, sizeof(double) * c->N, cudaMemcpyDeviceToHost,
+                                    c->stream));
+  if (u)
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(u, c->mom_u, sizeof(double) * c->N * c->D,
+                                    cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+  return check_status(c);
+}
+
+int lbm_error_norms(lbm_ctx *c, const double *u_ref, lbm_norms *out) {
+  if (!c || !out) return LBM_EINVAL;
+  cudaSetDevice(c->device);
+  const int nb = norm_blocks_for(c->N);
+  if (!c->partials) CUDA_OR_FAIL(c, cudaMalloc(&c->partials, sizeof(double) * kNormFields * nb));
+  if (!c->norm_out) CUDA_OR_FAIL(c, cudaMalloc(&c->norm_out, sizeof(double) * kNormFields));
+  if (!c->u_prev) {
+    CUDA_OR_FAIL(c, cudaMalloc(&c->u_prev, sizeof(double) * c->N * c->D));
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->u_prev, 0, sizeof(double) * c->N * c->D, c->stream));
+  }
+  if (u_ref) {
+    if (!c->u_ref) CUDA_OR_FAIL(c, cudaMalloc(&c->u_ref, sizeof(double) * c->N * c->D));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->u_ref, u_ref, sizeof(double) * c->N * c->D,
+                                    cudaMemcpyHostToDevice, c->stream));
+  }
+  CUDA_OR_FAIL(c, launch_norm_partials(c->lattice, c->precision, aux_args(c), (c->t & 1) != 0,
+                                       u_ref ? c->u_ref : nullptr, c->u_prev, c->partials, nb,
+                                       c->stream));
+  CUDA_OR_FAIL(c, launch_norm_finish(c->partials, nb, c->norm_out, c->stream));
+  double h[kNormFields];
+  CUDA_OR_FAIL(c, cudaMemcpyAsync(h, c->norm_out, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+  const double nan = std::nan("");
+  out->l2_rel = u_ref ? std::sqrt(h[0]) / std::sqrt(h[1]) : nan;
+  out->linf = u_ref ? h[2] : nan;
+  out->mass = h[3];
+  out->mom[0] = h[4]; out->mom[1] = h[5]; out->mom[2] = h[6];
+  out->residual = h[8] > 0 ? std::sqrt(h[7]) / std::sqrt(h[8]) : nan;
+  if (h[9] > 0) return fail(c, LBM_EDIVERGED, "%g non-finite densities", h[9]);
+  return check_status(c);
+}
+
+int lbm_query(const lbm_ctx *c, int *Q, int *D, int64_t *nodes, int64_t *fluid_nodes,
+              int64_t *links) {
+  if (!c) return LBM_EINVAL;
+  if (Q) *Q = c->Q;
+  if (D) *D = c->D;
+  if (nodes) *nodes = c->N;
+  if (fluid_nodes) *fluid_nodes = c->n_fluid;
+  if (links) *links = c->n_links;
+  return LBM_OK;
+}
+
+const char *lbm_last_error(const lbm_ctx *c) {
+  return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,83 @@
+// lbm_internal.h -- device argument blocks and launcher declarations shared by the
+// library's translation units (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+namespace lbm {
+
+// node classes stored one byte per node
+enum : uint8_t { kFluid = 0, kBoundary = 1, kSolid = 2 };
+
+// Geometry on the device.  Boundary nodes (fluid nodes with at least one cut link)
+// own a record b = bidx[n]: bmask[b] has bit d set when x_n + e_d is solid, and the
+// node's links occupy coef[boff[b] .. boff[b] + popcount(bmask[b]) - 1] in
+// ascending d.
+struct DevGeometry {
+  const uint8_t *cls = nullptr;
+  const int32_t *bidx = nullptr;
+  const uint32_t *bmask = nullptr;
+  const int32_t *boff = nullptr;
+  const void *coef = nullptr;      // 4 coefficients per link, compute type
+};
+
+// Per-link coefficients of Eq. 2.13 with b folded in: the new value of the
+// population i = opp(d) is (1-b) g_i + a g_d + bb g'_i + c g'_d + w.
+template <class C>
+struct alignas(4 * sizeof(C)) LinkCoef {
+  C a, bb, c, w;
+};
+
+template <class C>
+struct SweepArgs {
+  void *pop;                 // Q * N storage elements, population i of node n at i*N + n
+  long long N;               // nodes
+  int nx, ny, nz, sy, sz;
+  DevGeometry geo;
+  C sn[19];                  // s_k / |M_k|^2 for the non-conserved rows
+  C F[3];                    // rho0 g / |M_j|^2
+  C inv_rho0;
+  C one_minus_b;
+  int *status;               // bit 0: non-finite density seen
+};
+
+// launchers (return cudaGetLastError() of the launch)
+cudaError_t launch_sweep(int lattice, int precision, bool odd, const SweepArgs<double> &a64,
+                         const SweepArgs<float> &a32, cudaStream_t st);
+
+struct AuxArgs {
+  void *pop;
+  long long N;
+  int nx, ny, nz, sy, sz;
+  const uint8_t *cls;
+  double rho0;
+  double g[3];
+};
+
+// f = f^eq(rho, u) (deviation form) in the even-time layout; rho/u device or null
+cudaError_t launch_init_equilibrium(int lattice, int precision, const AuxArgs &a,
+                                    const double *rho, const double *u, cudaStream_t st);
+// full populations f[i*N+n] (double, device) <-> storage at time parity `odd`
+cudaError_t launch_get_populations(int lattice, int precision, const AuxArgs &a, bool odd,
+                                   double *f, cudaStream_t st);
+cudaError_t launch_set_populations(int lattice, int precision, const AuxArgs &a,
+                                   const double *f, cudaStream_t st);
+// rho (N) and u (D*N) in FP64 on the device; null pointers skip that output
+cudaError_t launch_moments(int lattice, int precision, const AuxArgs &a, bool odd, double *rho,
+                           double *u, cudaStream_t st);
+
+// Block partial sums of the error norms.  Layout of one partial record (doubles):
+// [0] sum |u_ref-u|^2, [1] sum |u_ref|^2, [2] max |u_ref-u|, [3] sum rho,
+// [4..6] sum j, [7] sum |u - u_prev|^2, [8] sum |u|^2, [9] non-finite count
+constexpr int kNormFields = 10;
+cudaError_t launch_norm_partials(int lattice, int precision, const AuxArgs &a, bool odd,
+                                 const double *u_ref, double *u_prev, double *partials,
+                                 int n_blocks, cudaStream_t st);
+cudaError_t launch_norm_finish(const double *partials, int n_blocks, double *out,
+                               cudaStream_t st);
+int norm_blocks_for(long long N);
+
+}  // namespace lbm

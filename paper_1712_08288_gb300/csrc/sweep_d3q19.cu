@@ -1,0 +1,18 @@
+// sweep_d3q19.cu -- D3Q19 instantiations of the fused collide / stream / boundary sweep
+// (storage: FP64, FP32 deviations, BF16 deviations, FP16 deviations).
+#include "sweep.cuh"
+
+namespace lbm {
+
+cudaError_t launch_sweep_d3q19(int precision, bool odd, const SweepArgs<double> &a64,
+                           const SweepArgs<float> &a32, cudaStream_t st) {
+  switch (precision) {
+    case 0: return launch_sweep_t<D3Q19, double>(odd, a64, st);
+    case 1: return launch_sweep_t<D3Q19, float>(odd, a32, st);
+    case 2: return launch_sweep_t<D3Q19, __nv_bfloat16>(odd, a32, st);
+    case 3: return launch_sweep_t<D3Q19, __half>(odd, a32, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace lbm
