@@ -163,6 +163,29 @@ typedef struct {
 } lbm_norms;
 int lbm_error_norms(lbm_ctx *ctx, const double *u_ref, lbm_norms *out);
 
+/* Error norms without any allocation.  There is no counterpart in the paper: this
+ * is a service entry point for callers that cannot allocate device memory when
+ * they need the norms -- applications that give the whole device to their own
+ * memory pool at start-up, services held to a fixed memory footprint, and tight
+ * monitoring loops that cannot take the implicit synchronisation of
+ * cudaMalloc/cudaFree.  It computes the same fluid-node sums as lbm_error_norms
+ * but keeps its block partial sums in a static device array of the library
+ * (80 KB, present on every GPU that loads the library until exit) and calls no
+ * allocating routine.
+ *   u_ref_dev  D*nodes doubles in device memory (node-major), or NULL to skip
+ *              l2_rel and linf (written as NaN).
+ *   out_dev    7 doubles in device memory, written on the context's stream:
+ *              l2_rel, linf, mass, mom[0..2], number of non-finite densities.
+ * No residual (it needs the per-context velocity history that lbm_error_norms
+ * allocates).  Asynchronous: nothing is read back; synchronise the stream before
+ * reading out_dev.
+ * Limit: at most 33,554,432 nodes (e.g. 322^3); larger grids return LBM_EINVAL.
+ * The first call on each device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents; calls
+ * that overlap on the GPU race on it, so issue them in order on one stream. */
+int lbm_error_norms_noalloc(lbm_ctx *ctx, const double *u_ref_dev, double *out_dev);
+
 /* Sizes: lattice Q and D, node counts, link count. */
 int lbm_query(const lbm_ctx *ctx, int *Q, int *D, int64_t *nodes, int64_t *fluid_nodes,
               int64_t *links);

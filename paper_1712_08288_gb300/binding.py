@@ -25,7 +25,7 @@ STATUS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA",
 EXPORTS = ["lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_set_skew", "lbm_set_geometry",
            "lbm_set_scheme", "lbm_set_force", "lbm_init_equilibrium", "lbm_set_populations",
            "lbm_get_populations", "lbm_step", "lbm_time", "lbm_moments", "lbm_moments_device",
-           "lbm_error_norms", "lbm_query", "lbm_last_error"]
+           "lbm_error_norms", "lbm_error_norms_noalloc", "lbm_query", "lbm_last_error"]
 
 
 class lbm_norms(ct.Structure):
@@ -54,6 +54,7 @@ def load_library(path=LIB_PATH):
         "lbm_moments": (I, [P, P, P]),
         "lbm_moments_device": (I, [P, P, P]),
         "lbm_error_norms": (I, [P, P, ct.POINTER(lbm_norms)]),
+        "lbm_error_norms_noalloc": (I, [P, P, P]),
         "lbm_query": (I, [P, P, P, P, P, P]),
         "lbm_last_error": (ct.c_char_p, [P]),
     }
@@ -186,6 +187,11 @@ class Lbm:
             self._check(rc)
         return dict(l2_rel=out.l2_rel, linf=out.linf, mass=out.mass, mom=list(out.mom),
                     residual=out.residual, status=rc)
+
+    def error_norms_noalloc(self, u_ref_dev_ptr, out_dev_ptr):
+        """lbm_error_norms_noalloc: device pointers in, nothing allocated, asynchronous."""
+        self._check(self._lib.lbm_error_norms_noalloc(self.h, ct.c_void_p(u_ref_dev_ptr),
+                                                      ct.c_void_p(out_dev_ptr)))
 
     def query(self):
         Q, D = ct.c_int(), ct.c_int()

@@ -22,6 +22,8 @@ cudaError_t launch_sweep_d2q9(int, bool, const SweepArgs<double> &, const SweepA
                               cudaStream_t);
 cudaError_t launch_sweep_d3q19(int, bool, const SweepArgs<double> &, const SweepArgs<float> &,
                                cudaStream_t);
+int error_norms_noalloc(int device, int lattice, int precision, const AuxArgs &a, bool odd,
+                        const double *u_ref, double *out, cudaStream_t st, const char **why);
 cudaError_t launch_sweep(int lattice, int precision, bool odd, const SweepArgs<double> &a64,
                          const SweepArgs<float> &a32, cudaStream_t st) {
   return lattice == LBM_D2Q9 ? launch_sweep_d2q9(precision, odd, a64, a32, st)
@@ -590,6 +592,15 @@ int lbm_error_norms(lbm_ctx *c, const double *u_ref, lbm_norms *out) {
   out->residual = h[8] > 0 ? std::sqrt(h[7]) / std::sqrt(h[8]) : nan;
   if (h[9] > 0) return fail(c, LBM_EDIVERGED, "%g non-finite densities", h[9]);
   return check_status(c);
+}
+
+int lbm_error_norms_noalloc(lbm_ctx *c, const double *u_ref_dev, double *out_dev) {
+  if (!c) return LBM_EINVAL;
+  const char *why = "";
+  const int rc = error_norms_noalloc(c->device, c->lattice, c->precision, aux_args(c),
+                                     (c->t & 1) != 0, u_ref_dev, out_dev, c->stream, &why);
+  if (rc != LBM_OK) return fail(c, rc, "lbm_error_norms_noalloc: %s", why);
+  return LBM_OK;
 }
 
 int lbm_query(const lbm_ctx *c, int *Q, int *D, int64_t *nodes, int64_t *fluid_nodes,
