@@ -13,14 +13,14 @@ namespace {
 
 template <class L>
 __device__ __forceinline__ long long slot(int i, long long n, bool odd, const AuxArgs &a) {
-  if (!odd) return (long long)i * a.N + n;
+  if (!odd) return (long long)i * a.S + n;
   const int x = (int)(n % a.nx);
   const long long r = n / a.nx;
   const int y = (int)(r % a.ny);
   const int z = (int)(r / a.ny);
   const long long nb =
       wrap_index(x, y, z, -L::ex(i), -L::ey(i), -L::ez(i), a.nx, a.ny, a.nz, a.sy, a.sz);
-  return (long long)L::opp(i) * a.N + nb;
+  return (long long)L::opp(i) * a.S + nb;
 }
 
 __device__ __forceinline__ double quiet_nan() { return __longlong_as_double(0x7ff8000000000000LL); }
@@ -31,7 +31,7 @@ __global__ void init_eq_kernel(AuxArgs a, const double *rho, const double *u) {
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < a.N;
        n += (long long)gridDim.x * blockDim.x) {
     if (a.cls[n] == kSolid) {
-      for (int i = 0; i < L::Q; ++i) Storage<T>::store(pop + (long long)i * a.N + n, 0.0);
+      for (int i = 0; i < L::Q; ++i) Storage<T>::store(pop + (long long)i * a.S + n, 0.0);
       continue;
     }
     const double drho = rho ? rho[n] - a.rho0 : 0.0;
@@ -47,7 +47,7 @@ __global__ void init_eq_kernel(AuxArgs a, const double *rho, const double *u) {
       const double cu = L::ex(i) * ux + L::ey(i) * uy + L::ez(i) * uz;
       // Eq. 42 minus w_i rho0, c_s^2 = 1/3
       const double geq = L::w(i) * (drho + a.rho0 * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2));
-      Storage<T>::store(pop + (long long)i * a.N + n, geq);
+      Storage<T>::store(pop + (long long)i * a.S + n, geq);
     }
   }
 }
@@ -76,7 +76,7 @@ __global__ void set_pop_kernel(AuxArgs a, const double *f) {
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
       const double v = solid ? 0.0 : f[(long long)i * a.N + n] - L::w(i) * a.rho0;
-      Storage<T>::store(pop + (long long)i * a.N + n, v);
+      Storage<T>::store(pop + (long long)i * a.S + n, v);
     }
   }
 }

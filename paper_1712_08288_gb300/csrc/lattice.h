@@ -40,6 +40,10 @@ struct D2Q9 {
     constexpr int t[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
     return t[i];
   }
+  // opp for a runtime index (no table): 1..4 and 5..8 are cycles of four
+  LBM_HD static constexpr int opp_rt(int i) {
+    return i == 0 ? 0 : (i < 5 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
+  }
   // weight w_i times 36
   LBM_HD static constexpr int w36(int i) { return i == 0 ? 16 : (i < 5 ? 4 : 1); }
   LBM_HD static constexpr double w(int i) { return w36(i) / 36.0; }
@@ -85,6 +89,7 @@ struct D3Q19 {
     return t[i];
   }
   LBM_HD static constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+  LBM_HD static constexpr int opp_rt(int i) { return opp(i); }
   LBM_HD static constexpr int w36(int i) {
     return i == 0 ? 12 : (i < 7 ? 2 : 1);
   }
@@ -119,6 +124,27 @@ struct D3Q19 {
   static constexpr int kNormJ = 10;
 };
 
+// Runtime (non-constant index) access to the velocity components and opposites,
+// from bit masks built at compile time, so that no table lands in local memory.
+template <class L>
+constexpr unsigned comp_mask(int comp, int sign) {
+  unsigned m = 0;
+  for (int i = 0; i < L::Q; ++i) {
+    const int v = comp == 0 ? L::ex(i) : (comp == 1 ? L::ey(i) : L::ez(i));
+    if (v == sign) m |= 1u << i;
+  }
+  return m;
+}
+template <class L>
+struct DirBits {
+  static constexpr unsigned kXp = comp_mask<L>(0, 1), kXn = comp_mask<L>(0, -1);
+  static constexpr unsigned kYp = comp_mask<L>(1, 1), kYn = comp_mask<L>(1, -1);
+  static constexpr unsigned kZp = comp_mask<L>(2, 1), kZn = comp_mask<L>(2, -1);
+  LBM_HD static int ex(int i) { return (int)((kXp >> i) & 1u) - (int)((kXn >> i) & 1u); }
+  LBM_HD static int ey(int i) { return (int)((kYp >> i) & 1u) - (int)((kYn >> i) & 1u); }
+  LBM_HD static int ez(int i) { return (int)((kZp >> i) & 1u) - (int)((kZn >> i) & 1u); }
+};
+
 // squared norm of row k: sum_i M(k,i)^2
 template <class L>
 LBM_HD constexpr int row_norm2(int k) {
@@ -148,6 +174,8 @@ LBM_HD constexpr bool row_is_even(int k) {
 }
 template <class L>
 constexpr bool lattice_is_consistent() {
+  for (int i = 0; i < L::Q; ++i)
+    if (L::opp_rt(i) != L::opp(i)) return false;
   // every row has a parity, rows are orthogonal, pairs cover every moving direction
   for (int k = 0; k < L::Q; ++k)
     if (row_is_odd<L>(k) == row_is_even<L>(k)) return false;

@@ -19,15 +19,16 @@
 
 namespace lbm {
 cudaError_t launch_sweep_d2q9(int, bool, const SweepArgs<double> &, const SweepArgs<float> &,
-                              cudaStream_t);
+                              const int4 *, int, int, cudaStream_t);
 cudaError_t launch_sweep_d3q19(int, bool, const SweepArgs<double> &, const SweepArgs<float> &,
-                               cudaStream_t);
+                               const int4 *, int, int, cudaStream_t);
 int error_norms_noalloc(int device, int lattice, int precision, const AuxArgs &a, bool odd,
                         const double *u_ref, double *out, cudaStream_t st, const char **why);
 cudaError_t launch_sweep(int lattice, int precision, bool odd, const SweepArgs<double> &a64,
-                         const SweepArgs<float> &a32, cudaStream_t st) {
-  return lattice == LBM_D2Q9 ? launch_sweep_d2q9(precision, odd, a64, a32, st)
-                             : launch_sweep_d3q19(precision, odd, a64, a32, st);
+                         const SweepArgs<float> &a32, const int4 *tiles, int n_tiles, int bx,
+                         cudaStream_t st) {
+  return lattice == LBM_D2Q9 ? launch_sweep_d2q9(precision, odd, a64, a32, tiles, n_tiles, bx, st)
+                             : launch_sweep_d3q19(precision, odd, a64, a32, tiles, n_tiles, bx, st);
 }
 }  // namespace lbm
 
@@ -48,7 +49,8 @@ struct lbm_ctx {
   bool geometry_set = false;
 
   // device buffers
-  void *pop = nullptr;
+  void *pop_alloc = nullptr;    // populations with kPopPadBytes on both sides
+  void *pop = nullptr;          // = pop_alloc + kPopPadBytes
   uint8_t *cls = nullptr;
   int32_t *bidx = nullptr;
   uint32_t *bmask = nullptr;
@@ -61,6 +63,9 @@ struct lbm_ctx {
   double *u_prev = nullptr;
   double *mom_rho = nullptr;
   double *mom_u = nullptr;
+  int4 *tiles = nullptr;        // active tiles of the sweep
+  int n_tiles = 0;
+  int bx = 128;                 // tile width = threads per block
 
   // host copy of the cut links in device order (for re-deriving coefficients)
   std::vector<int32_t> link_dir;
@@ -98,6 +103,10 @@ static int store_bytes(int precision) {
   return precision == LBM_F64 ? 8 : (precision == LBM_F32_DEV ? 4 : 2);
 }
 
+static size_t pop_alloc_bytes(const lbm_ctx *c) {
+  return (size_t)c->Q * slot_stride(c->N) * store_bytes(c->precision) + 2 * kPopPadBytes;
+}
+
 template <class F>
 static auto with_lat(int lattice, F &&f) {
   return lattice == LBM_D2Q9 ? f(D2Q9{}) : f(D3Q19{});
@@ -116,6 +125,7 @@ static AuxArgs aux_args(const lbm_ctx *c) {
   AuxArgs a;
   a.pop = c->pop;
   a.N = c->N;
+  a.S = slot_stride(c->N);
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.sy = c->sy; a.sz = c->sz;
   a.cls = c->cls;
   a.rho0 = c->rho0;
@@ -131,6 +141,7 @@ static void refresh_args(lbm_ctx *c) {
     using C = std::remove_reference_t<decltype(a.inv_rho0)>;
     a.pop = c->pop;
     a.N = c->N;
+    a.S = slot_stride(c->N);
     a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.sy = c->sy; a.sz = c->sz;
     a.geo = geo;
     with_lat(c->lattice, [&](auto lat) {
@@ -145,6 +156,16 @@ static void refresh_args(lbm_ctx *c) {
     a.inv_rho0 = C(1.0 / c->rho0);
     a.one_minus_b = C(1.0 - c->b);
     a.status = c->status;
+    with_lat(c->lattice, [&](auto lat) {
+      using L = decltype(lat);
+      const long long S = slot_stride(c->N), nxl = c->nx, nxy = (long long)c->nx * c->ny;
+      for (int i = 0; i < 19; ++i) a.koff_even[i] = a.koff_odd[i] = 0;
+      for (int i = 0; i < L::Q; ++i) {
+        a.koff_even[i] = L::opp(i) * S;
+        a.koff_odd[i] = i * S + L::ex(i) + nxl * L::ey(i) + nxy * L::ez(i);
+      }
+      return 0;
+    });
   };
   fill(c->a64);
   fill(c->a32);
@@ -204,6 +225,31 @@ static void free_geometry(lbm_ctx *c) {
   cudaFree(c->coef); c->coef = nullptr;
 }
 
+// Tiles (x0, y, z) of bx consecutive nodes along x that hold at least one fluid
+// node; solid-only runs are never launched.  solid == nullptr: all fluid.
+static int upload_tiles(lbm_ctx *c, const uint8_t *solid) {
+  c->bx = 32;   // one warp per tile
+  const int nxb = (c->nx + c->bx - 1) / c->bx;
+  std::vector<int4> t;
+  t.reserve((size_t)nxb * c->ny * c->nz);
+  for (int z = 0; z < c->nz; ++z)
+    for (int y = 0; y < c->ny; ++y)
+      for (int xb = 0; xb < nxb; ++xb) {
+        const int x0 = xb * c->bx, x1 = std::min(c->nx, x0 + c->bx);
+        bool any = solid == nullptr;
+        const long long row = (long long)c->nx * (y + (long long)c->ny * z);
+        for (int x = x0; x < x1 && !any; ++x) any = solid[row + x] == 0;
+        if (any) t.push_back(make_int4(x0, y, z, 0));
+      }
+  cudaFree(c->tiles);
+  c->tiles = nullptr;
+  c->n_tiles = (int)t.size();
+  if (t.empty()) return LBM_OK;
+  CUDA_OR_FAIL(c, cudaMalloc((void **)&c->tiles, sizeof(int4) * t.size()));
+  CUDA_OR_FAIL(c, cudaMemcpy(c->tiles, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice));
+  return LBM_OK;
+}
+
 extern "C" {
 
 int lbm_create(lbm_ctx **out, int lattice, int nx, int ny, int nz, const double *s,
@@ -236,11 +282,12 @@ int lbm_create(lbm_ctx **out, int lattice, int nx, int ny, int nz, const double 
   c->rho0 = rho0;
   for (int k = 0; k < Q; ++k) c->s[k] = s[k];
   cudaError_t e = cudaGetDevice(&c->device);
-  size_t pop_bytes = (size_t)Q * N * store_bytes(precision);
-  if (e == cudaSuccess) e = cudaMalloc(&c->pop, pop_bytes);
+  const size_t pop_bytes = pop_alloc_bytes(c);
+  if (e == cudaSuccess) e = cudaMalloc(&c->pop_alloc, pop_bytes);
+  if (e == cudaSuccess) c->pop = static_cast<char *>(c->pop_alloc) + kPopPadBytes;
   if (e == cudaSuccess) e = cudaMalloc((void **)&c->cls, N);
   if (e == cudaSuccess) e = cudaMalloc((void **)&c->status, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(c->pop, 0, pop_bytes);
+  if (e == cudaSuccess) e = cudaMemset(c->pop_alloc, 0, pop_bytes);
   if (e == cudaSuccess) e = cudaMemset(c->cls, kFluid, N);
   if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int));
   if (e != cudaSuccess) {
@@ -251,6 +298,11 @@ int lbm_create(lbm_ctx **out, int lattice, int nx, int ny, int nz, const double 
   }
   c->n_fluid = N;
   c->geometry_set = true;  // all-fluid periodic box, no links
+  if (upload_tiles(c, nullptr) != LBM_OK) {
+    g_create_error = c->err;
+    lbm_destroy(c);
+    return LBM_ECUDA;
+  }
   refresh_args(c);
   *out = c;
   return LBM_OK;
@@ -260,7 +312,7 @@ int lbm_destroy(lbm_ctx *c) {
   if (!c) return LBM_OK;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
-  cudaFree(c->pop);
+  cudaFree(c->pop_alloc);
   cudaFree(c->cls);
   cudaFree(c->status);
   free_geometry(c);
@@ -270,6 +322,7 @@ int lbm_destroy(lbm_ctx *c) {
   cudaFree(c->u_prev);
   cudaFree(c->mom_rho);
   cudaFree(c->mom_u);
+  cudaFree(c->tiles);
   delete c;
   return LBM_OK;
 }
@@ -413,7 +466,8 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *solid, int64_t n_links, const in
                                cudaMemcpyHostToDevice));
   }
   if ((rc = upload_coefficients(c)) != LBM_OK) return rc;
-  CUDA_OR_FAIL(c, cudaMemset(c->pop, 0, (size_t)c->Q * N * store_bytes(c->precision)));
+  if ((rc = upload_tiles(c, solid)) != LBM_OK) return rc;
+  CUDA_OR_FAIL(c, cudaMemset(c->pop_alloc, 0, pop_alloc_bytes(c)));
   CUDA_OR_FAIL(c, cudaMemset(c->status, 0, sizeof(int)));
   cudaFree(c->u_prev);
   c->u_prev = nullptr;
@@ -520,7 +574,7 @@ int lbm_step(lbm_ctx *c, int n) {
   if (!c->geometry_set) return fail(c, LBM_ESTATE, "lbm_step: geometry not set");
   for (int k = 0; k < n; ++k) {
     const cudaError_t e = launch_sweep(c->lattice, c->precision, (c->t & 1) != 0, c->a64, c->a32,
-                                       c->stream);
+                                       c->tiles, c->n_tiles, c->bx, c->stream);
     if (e != cudaSuccess) return fail(c, LBM_ECUDA, "lbm_step: %s", cudaGetErrorString(e));
     ++c->t;
   }
@@ -533,7 +587,8 @@ static int check_status(lbm_ctx *c) {
   int h = 0;
   CUDA_OR_FAIL(c, cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
-  if (h) return fail(c, LBM_EDIVERGED, "a non-finite or runaway density was seen");
+  if (h & 2) return fail(c, LBM_ETIMEOUT, "a sweep gave up waiting for a bulk copy (bounded wait)");
+  if (h & 1) return fail(c, LBM_EDIVERGED, "a non-finite or runaway density was seen");
   return LBM_OK;
 }
 

@@ -31,26 +31,41 @@ struct alignas(4 * sizeof(C)) LinkCoef {
   C a, bb, c, w;
 };
 
+// Populations: Q slots of S >= N storage elements each (S a multiple of 64),
+// population i of node n at pop[i*S + n].  The allocation extends kPopPadBytes
+// before pop and after the last slot, so that aligned bulk copies of a row window
+// may start a little before a row or end a little after it.
+constexpr long long kPopPadBytes = 4096;
+inline long long slot_stride(long long N) { return (N + 63) / 64 * 64; }
+
 template <class C>
 struct SweepArgs {
-  void *pop;                 // Q * N storage elements, population i of node n at i*N + n
+  void *pop;                 // population i of node n at pop[i*S + n]
   long long N;               // nodes
+  long long S;               // slot stride
   int nx, ny, nz, sy, sz;
   DevGeometry geo;
   C sn[19];                  // s_k / |M_k|^2 for the non-conserved rows
   C F[3];                    // rho0 g / |M_j|^2
   C inv_rho0;
   C one_minus_b;
-  int *status;               // bit 0: non-finite density seen
+  int *status;               // bit 0: non-finite density seen, bit 1: bounded wait gave up
+  // element offsets of the stores of an interior node: even step slot opp(i) of
+  // the node itself, odd step slot i of x + e_i (no wrap)
+  long long koff_even[19];
+  long long koff_odd[19];
 };
 
 // launchers (return cudaGetLastError() of the launch)
+// tiles: n_tiles runs (x0, y, z) of bx nodes along x holding at least one fluid node
 cudaError_t launch_sweep(int lattice, int precision, bool odd, const SweepArgs<double> &a64,
-                         const SweepArgs<float> &a32, cudaStream_t st);
+                         const SweepArgs<float> &a32, const int4 *tiles, int n_tiles, int bx,
+                         cudaStream_t st);
 
 struct AuxArgs {
   void *pop;
-  long long N;
+  long long N;               // nodes
+  long long S;               // slot stride
   int nx, ny, nz, sy, sz;
   const uint8_t *cls;
   double rho0;

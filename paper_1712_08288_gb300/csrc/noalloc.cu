@@ -50,9 +50,9 @@ __global__ void __launch_bounds__(kNoAllocThreads)
     double drho = 0.0, j[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-      long long s = (long long)i * a.N + n;                 // even time: own slot i
+      long long s = (long long)i * a.S + n;                 // even time: own slot i
       if (odd)                                              // odd time: slot opp(i) of x - e_i
-        s = (long long)L::opp(i) * a.N +
+        s = (long long)L::opp(i) * a.S +
             wrap_index(x, y, z, -L::ex(i), -L::ey(i), -L::ez(i), a.nx, a.ny, a.nz, a.sy, a.sz);
       const double g = (double)Storage<T>::load(pop + s);
       drho += g;

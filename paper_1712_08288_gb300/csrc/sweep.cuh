@@ -172,95 +172,363 @@ __device__ __forceinline__ void collide(const C (&g)[L::Q], C (&gp)[L::Q], const
   }
 }
 
-template <class L, class T, bool ODD>
-__global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs<typename Storage<T>::C> a) {
+// Wrap an index that is at most one period outside [0, n).
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// Linear index of the neighbour x + e_k (periodic, x-wrap skewed by (sy, sz) when
+// SKEW).  The per-node part (wrapped x +- 1 and the skew-shifted rows) is computed
+// once; per direction, row coordinates are wrapped only where that direction can
+// leave the range, which the compiler resolves at compile time.
+template <class L, bool SKEW>
+struct Neighbours {
+  int x, y, z, xm, xp, ym, yp, zm, zp, nx, ny, nz;
+  __device__ __forceinline__ Neighbours(int x_, int y_, int z_, int nx_, int ny_, int nz_, int sy,
+                                        int sz)
+      : x(x_), y(y_), z(z_), nx(nx_), ny(ny_), nz(nz_) {
+    xm = x - 1;
+    xp = x + 1;
+    const bool cm = xm < 0, cp = xp >= nx;
+    if (cm) xm += nx;
+    if (cp) xp -= nx;
+    ym = yp = y;
+    zm = zp = z;
+    if (SKEW) {
+      // crossing x = 0 downward lands at (nx-1, y+sy, z+sz); crossing x = nx-1 upward
+      // lands at (0, y-sy, z-sz) (the field is invariant under (nx, sy, sz))
+      if (cm) { ym += sy; zm += sz; }
+      if (cp) { yp -= sy; zp -= sz; }
+    }
+  }
+  __device__ __forceinline__ int operator()(int k) const {
+    const int ex = L::ex(k), ey = L::ey(k), ez = L::ez(k);
+    const int xx = ex < 0 ? xm : (ex > 0 ? xp : x);
+    int yy = (ex < 0 ? ym : (ex > 0 ? yp : y)) + ey;
+    if (ey != 0 || (SKEW && ex != 0)) yy = wrap1(yy, ny);
+    int zz = 0;
+    if (L::D == 3) {
+      zz = (ex < 0 ? zm : (ex > 0 ? zp : z)) + ez;
+      if (ez != 0 || (SKEW && ex != 0)) zz = wrap1(zz, nz);
+    }
+    return xx + nx * (yy + ny * zz);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Bulk-copy pipeline helpers (inline PTX, sm_90+): mbarrier with transaction
+// count, cp.async.bulk global -> shared.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// bounded wait: false after kWaitLimit polls (each poll may suspend briefly)
+constexpr int kWaitLimit = 1 << 20;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+  for (int it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes,
+                                              uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Work decomposition.  A tile is a run of kTileW = 32 nodes along x that holds at
+// least one fluid node; tiles are listed once per geometry.  Every warp owns a
+// private pipeline of kStages shared-memory stages: stage s holds the Q population
+// row windows of one tile (each window up to kTileW + 16/sizeof(T) elements, start
+// aligned down to 16 bytes), filled by bulk copies that complete on the warp's own
+// mbarrier.  Warps never wait for each other.
+constexpr int kTileW = 32;
+constexpr int kWarpsPerBlock = 4;
+
+#ifndef LBM_STAGES_4B
+#define LBM_STAGES_4B 2
+#endif
+template <class T>
+struct StageShape {
+  static constexpr int kStages = sizeof(T) == 8 ? 2 : (sizeof(T) == 4 ? LBM_STAGES_4B : 3);
+  static constexpr int kWidth = kTileW + 16 / (int)sizeof(T);   // elements per window
+};
+
+// bytes of one warp's pipeline (stages, barriers, offsets), a multiple of 128 so
+// that every warp's stages start 128-byte aligned
+template <class L, class T>
+__host__ __device__ constexpr size_t warp_smem_bytes() {
+  return ((size_t)StageShape<T>::kStages * L::Q * StageShape<T>::kWidth * sizeof(T) +
+          StageShape<T>::kStages * (sizeof(uint64_t) + L::Q * sizeof(int)) + 127) / 128 * 128;
+}
+static_assert(warp_smem_bytes<D3Q19, float>() % 128 == 0, "warp region alignment");
+static_assert((StageShape<float>::kWidth * sizeof(float)) % 16 == 0, "window stride");
+static_assert((StageShape<double>::kWidth * sizeof(double)) % 16 == 0, "window stride");
+static_assert((StageShape<__half>::kWidth * sizeof(__half)) % 16 == 0, "window stride");
+
+// Lanes 0..Q-1 of a warp fill one stage with the row windows of a tile, lane i
+// copying population i: in an even step the window [x0, x0+32) of slot i in the
+// tile's own row; in an odd step [x0 - ex_i, x0 - ex_i + 32) of slot opp(i) in row
+// (y - ey_i, z - ez_i).  Each copy starts at the 16-byte boundary at or before the
+// first element and covers the window rounded up to 16 bytes; off[i] records where
+// the tile's first element landed.  The offsets are stored before lane 0's arrive
+// (release), so a lane that has waited on the barrier sees them.  All 32 lanes call.
+template <class L, class T, bool ODD, class I>
+__device__ __forceinline__ void issue_tile(const SweepArgs<typename Storage<T>::C> &a, int4 tl,
+                                           T *stage, int *off, uint64_t *bar) {
+  constexpr int W = StageShape<T>::kWidth;
+  const int lane = threadIdx.x & 31;
+  const char *pa = nullptr;
+  uint32_t bytes = 0;
+  if (lane < L::Q) {
+    const int i = lane;
+    int slot = i, yy = tl.y, zz = tl.z, xs = tl.x;
+    if (ODD) {
+      slot = L::opp_rt(i);
+      yy = wrap1(tl.y - DirBits<L>::ey(i), a.ny);
+      zz = (L::D == 3) ? wrap1(tl.z - DirBits<L>::ez(i), a.nz) : 0;
+      xs = tl.x - DirBits<L>::ex(i);
+    }
+    const I elem = (I)slot * (I)a.S + (I)a.nx * ((I)yy + (I)a.ny * zz) + xs;
+    const char *p = static_cast<const char *>(a.pop) + (long long)elem * (long long)sizeof(T);
+    pa = reinterpret_cast<const char *>(reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)15);
+    const int delta = (int)((p - pa) / (long long)sizeof(T));
+    off[i] = delta;
+    bytes = ((uint32_t)((delta + kTileW) * (int)sizeof(T)) + 15u) & ~15u;
+  }
+  const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
+  __syncwarp();
+  if (lane == 0) mbar_arrive_expect_tx(bar, total);
+  __syncwarp();
+  if (lane < L::Q) bulk_copy_g2s(stage + lane * W, pa, bytes, bar);
+}
+
+// resident blocks per SM the register budget is sized for
+#ifndef LBM_MINBLOCKS_F32
+#define LBM_MINBLOCKS_F32 8
+#endif
+template <class T>
+struct MinBlocks {
+  static constexpr int value = LBM_MINBLOCKS_F32;   // 8 x 128 threads: 64 registers
+};
+template <>
+struct MinBlocks<double> {
+  static constexpr int value = 4;   // 4 x 128 threads: 128 registers (FP64 arithmetic)
+};
+
+// One fused time step.  Persistent warps: global warp w handles tiles
+// w, w + W_total, ...  I is the index type of a population slot (int when
+// Q*S < 2^31, else long long).
+// Shared-memory offset of a window's first element when every row starts on a
+// 16-byte boundary (nx*sizeof(T) % 16 == 0): the copy of an odd-step window that
+// begins at x0 - ex starts 16/sizeof(T) - 1 elements early for ex = +1, one element
+// early for ex = -1, exactly for ex = 0.
+template <class T>
+__device__ __forceinline__ constexpr int aligned_window_offset(int ex) {
+  return ex > 0 ? 16 / (int)sizeof(T) - 1 : (ex < 0 ? 1 : 0);
+}
+
+template <class L, class T, bool ODD, bool SKEW, bool ALIGNED, class I>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
+    sweep_kernel(const SweepArgs<typename Storage<T>::C> a, const int4 *__restrict__ tiles,
+                 int n_tiles) {
   using C = typename Storage<T>::C;
   constexpr int Q = L::Q;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= a.nx) return;
-  const int y = blockIdx.y, z = blockIdx.z;
-  const long long N = a.N;
-  const long long n = x + (long long)a.nx * (y + (long long)a.ny * z);
-  const uint8_t cls = __ldg(a.geo.cls + n);
-  if (cls == kSolid) return;
+  constexpr int NS = StageShape<T>::kStages;
+  constexpr int W = StageShape<T>::kWidth;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char *wsm = smem_raw + (size_t)warp * warp_smem_bytes<L, T>();
+  T *stages = reinterpret_cast<T *>(wsm);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + (size_t)NS * Q * W * sizeof(T));
+  int *offs = reinterpret_cast<int *>(bars + NS);
+
+  const int gw = blockIdx.x * kWarpsPerBlock + warp;
+  const int nw = gridDim.x * kWarpsPerBlock;
+  if (lane == 0) {
+    for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  for (int s = 0; s < NS; ++s) {
+    const int tile = gw + s * nw;
+    if (tile < n_tiles) issue_tile<L, T, ODD, I>(a, tiles[tile], stages + s * Q * W, offs + s * Q, &bars[s]);
+  }
+  const int nxm1 = a.nx - 1;
+
   T *__restrict__ pop = static_cast<T *>(a.pop);
-  const bool interior = x > 0 && x < a.nx - 1 && y > 0 && y < a.ny - 1 &&
-                        (L::D == 2 || (z > 0 && z < a.nz - 1));
-  const long long sx = 1, syy = a.nx, szz = (long long)a.nx * a.ny;
-
-  C g[Q];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    long long src;
-    if (!ODD) {
-      src = (long long)i * N + n;
-    } else {
-      const long long nb =
-          interior ? n - (L::ex(i) * sx + L::ey(i) * syy + L::ez(i) * szz)
-                   : wrap_index(x, y, z, -L::ex(i), -L::ey(i), -L::ez(i), a.nx, a.ny, a.nz, a.sy,
-                                a.sz);
-      src = (long long)L::opp(i) * N + nb;
+  const I S = (I)a.S;
+  int k = 0;
+  for (int tile = gw; tile < n_tiles; tile += nw, ++k) {
+    const int s = k % NS;
+    const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)(k / NS) & 1u);
+    if (__any_sync(0xffffffffu, !ok)) {
+      // a copy did not land in time: flag it, drain what this warp issued, stop
+      if (lane == 0) atomicOr(a.status, 2);
+      for (int j = 0; j < NS; ++j)
+        if (tile + j * nw < n_tiles) mbar_wait_bounded(&bars[(k + j) % NS], (uint32_t)((k + j) / NS) & 1u);
+      return;
     }
-    g[i] = Storage<T>::load(pop + src);
-  }
-
-  C gp[Q];
-  C drho;
-  collide<L, C>(g, gp, a, drho);
-  if (!(fabs(drho) < C(1e6))) atomicOr(a.status, 1);
-
-  // stream
+    const int4 tl = tiles[tile];
+    const int x = tl.x + lane;
+    const int y = tl.y, z = tl.z;
+    const bool in_row = x < a.nx;
+    const int n = in_row ? x + a.nx * (y + a.ny * z) : 0;
+    const uint8_t cls = in_row ? __ldg(a.geo.cls + n) : (uint8_t)kSolid;
+    const T *st = stages + s * Q * W;
+    C g[Q];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    long long dst;
-    if (!ODD) {
-      dst = (long long)L::opp(i) * N + n;
-    } else {
-      const long long nb =
-          interior ? n + (L::ex(i) * sx + L::ey(i) * syy + L::ez(i) * szz)
-                   : wrap_index(x, y, z, L::ex(i), L::ey(i), L::ez(i), a.nx, a.ny, a.nz, a.sy,
-                                a.sz);
-      dst = (long long)i * N + nb;
+    for (int i = 0; i < Q; ++i) {
+      const int o = ALIGNED ? (ODD ? aligned_window_offset<T>(L::ex(i)) : 0) : offs[s * Q + i];
+      g[i] = Storage<T>::load(st + i * W + o + lane);
     }
-    Storage<T>::store(pop + dst, gp[i]);
-  }
+    __syncwarp();   // stage s consumed: refill it with the tile NS rounds ahead
+    {
+      const int nt = tile + NS * nw;
+      if (nt < n_tiles) issue_tile<L, T, ODD, I>(a, tiles[nt], stages + s * Q * W, offs + s * Q, &bars[s]);
+    }
+    if (cls == kSolid) continue;
 
-  // single-node boundary scheme on the cut links of this node (Eqs. 2.10, 2.13)
-  if (cls == kBoundary) {
-    const int b = __ldg(a.geo.bidx + n);
-    const uint32_t mask = __ldg(a.geo.bmask + b);
-    const int off = __ldg(a.geo.boff + b);
-    const LinkCoef<C> *coef = static_cast<const LinkCoef<C> *>(a.geo.coef);
+    // lanes on the periodic x-edges: the row windows cannot follow the wrap
+    const bool xlo = ODD && x == 0, xhi = ODD && x == nxm1;
+    if (ODD && (xlo || xhi)) {
 #pragma unroll
-    for (int dd = 1; dd < Q; ++dd) {
-      if (mask & (1u << dd)) {
-        const LinkCoef<C> c = coef[off + __popc(mask & ((1u << dd) - 1u))];
-        const int i = L::opp(dd);
-        const C v = a.one_minus_b * g[i] + c.a * g[dd] + c.bb * gp[i] + c.c * gp[dd] + c.w;
-        long long dst;
-        if (!ODD) {
-          // slot dd of the solid neighbour x_f + e_dd
-          const long long nb =
-              interior ? n + (L::ex(dd) * sx + L::ey(dd) * syy + L::ez(dd) * szz)
-                       : wrap_index(x, y, z, L::ex(dd), L::ey(dd), L::ez(dd), a.nx, a.ny, a.nz,
-                                    a.sy, a.sz);
-          dst = (long long)dd * N + nb;
-        } else {
-          dst = (long long)i * N + n;
+      for (int i = 0; i < Q; ++i) {
+        const int ex = L::ex(i);
+        if ((ex > 0 && xlo) || (ex < 0 && xhi)) {
+          const long long src = wrap_index(x, y, z, -ex, -L::ey(i), -L::ez(i), a.nx, a.ny, a.nz,
+                                           a.sy, a.sz);
+          g[i] = Storage<T>::load(pop + (I)L::opp(i) * S + (I)src);
         }
-        Storage<T>::store(pop + dst, v);
+      }
+    }
+
+    C gp[Q];
+    C drho;
+    collide<L, C>(g, gp, a, drho);
+    if (!(fabs(drho) < C(1e6))) atomicOr(a.status, 1);
+
+    T *const pn = pop + n;
+    if (!ODD) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) Storage<T>::store(pn + (I)a.koff_even[i], gp[i]);   // slot opp(i) of x
+    } else {
+      // rows y +- 1, z +- 1 stay inside the grid for the whole tile: constant offsets
+      const bool rows_inside =
+          y > 0 && y < a.ny - 1 && (L::D == 2 || (z > 0 && z < a.nz - 1));
+      if (rows_inside) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          const int ex = L::ex(i);
+          if ((ex > 0 && xhi) || (ex < 0 && xlo)) continue;   // crosses the x-wrap
+          Storage<T>::store(pn + (I)a.koff_odd[i], gp[i]);     // slot i of x + e_i
+        }
+        if (xlo || xhi) {
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            const int ex = L::ex(i);
+            if ((ex > 0 && xhi) || (ex < 0 && xlo)) {
+              const long long dn = wrap_index(x, y, z, ex, L::ey(i), L::ez(i), a.nx, a.ny, a.nz,
+                                              a.sy, a.sz);
+              Storage<T>::store(pop + (I)i * S + (I)dn, gp[i]);
+            }
+          }
+        }
+      } else {
+        const Neighbours<L, SKEW> nb(x, y, z, a.nx, a.ny, a.nz, a.sy, a.sz);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Storage<T>::store(pop + (I)i * S + (I)nb(i), gp[i]);
+      }
+    }
+
+    // single-node boundary scheme on the cut links of this node (Eqs. 2.10, 2.13)
+    if (cls == kBoundary) {
+      const int b = __ldg(a.geo.bidx + n);
+      const uint32_t mask = __ldg(a.geo.bmask + b);
+      const int off = __ldg(a.geo.boff + b);
+      const LinkCoef<C> *coef = static_cast<const LinkCoef<C> *>(a.geo.coef);
+#pragma unroll
+      for (int dd = 1; dd < Q; ++dd) {
+        if (mask & (1u << dd)) {
+          const LinkCoef<C> c = coef[off + __popc(mask & ((1u << dd) - 1u))];
+          const int i = L::opp(dd);
+          const C v = a.one_minus_b * g[i] + c.a * g[dd] + c.bb * gp[i] + c.c * gp[dd] + c.w;
+          I dst;
+          if (!ODD) {
+            // slot dd of the solid neighbour x_f + e_dd (read there by the next odd step)
+            const long long sn = wrap_index(x, y, z, L::ex(dd), L::ey(dd), L::ez(dd), a.nx, a.ny,
+                                            a.nz, a.sy, a.sz);
+            dst = (I)dd * S + (I)sn;
+          } else {
+            dst = (I)i * S + (I)n;   // slot i of x_f itself (read there by the next even step)
+          }
+          Storage<T>::store(pop + dst, v);
+        }
       }
     }
   }
 }
 
+// persistent grid size per kernel instantiation: resident blocks per SM x SMs
+template <class K>
+int persistent_blocks(K kernel, int bx, size_t smem) {
+  static int cached = 0;
+  if (cached == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, bx, smem);
+    cached = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  }
+  return cached;
+}
+
 template <class L, class T>
-cudaError_t launch_sweep_t(bool odd, const SweepArgs<typename Storage<T>::C> &a, cudaStream_t st) {
-  const int bx = a.nx >= 128 ? 128 : (a.nx >= 64 ? 64 : 32);
-  dim3 block(bx, 1, 1);
-  dim3 grid((a.nx + bx - 1) / bx, a.ny, a.nz);
-  if (odd) sweep_kernel<L, T, true><<<grid, block, 0, st>>>(a);
-  else sweep_kernel<L, T, false><<<grid, block, 0, st>>>(a);
+cudaError_t launch_sweep_t(bool odd, const SweepArgs<typename Storage<T>::C> &a, const int4 *tiles,
+                           int n_tiles, int bx, cudaStream_t st) {
+  if (n_tiles == 0) return cudaSuccess;
+  const bool skew = a.sy != 0 || a.sz != 0;
+  const bool big = (long long)L::Q * a.S >= (1LL << 31);
+  const size_t smem = kWarpsPerBlock * warp_smem_bytes<L, T>();
+  const int threads = kWarpsPerBlock * 32;
+  (void)bx;
+  const bool aligned = ((long long)a.nx * (long long)sizeof(T)) % 16 == 0;
+#define LBM_LAUNCH(O, S, I)                                                        \
+  do {                                                                             \
+    auto kern = aligned ? sweep_kernel<L, T, O, S, true, I> : sweep_kernel<L, T, O, S, false, I>; \
+    int grid = persistent_blocks(kern, threads, smem);                             \
+    const int need = (n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;              \
+    if (grid > need) grid = need;                                                  \
+    kern<<<grid, threads, smem, st>>>(a, tiles, n_tiles);                          \
+  } while (0)
+  if (big) {
+    if (odd) { if (skew) LBM_LAUNCH(true, true, long long); else LBM_LAUNCH(true, false, long long); }
+    else LBM_LAUNCH(false, false, long long);
+  } else {
+    if (odd) { if (skew) LBM_LAUNCH(true, true, int); else LBM_LAUNCH(true, false, int); }
+    else LBM_LAUNCH(false, false, int);
+  }
+#undef LBM_LAUNCH
   return cudaGetLastError();
 }
 

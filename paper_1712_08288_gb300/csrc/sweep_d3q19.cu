@@ -5,12 +5,13 @@
 namespace lbm {
 
 cudaError_t launch_sweep_d3q19(int precision, bool odd, const SweepArgs<double> &a64,
-                           const SweepArgs<float> &a32, cudaStream_t st) {
+                           const SweepArgs<float> &a32, const int4 *tiles, int n_tiles,
+                           int bx, cudaStream_t st) {
   switch (precision) {
-    case 0: return launch_sweep_t<D3Q19, double>(odd, a64, st);
-    case 1: return launch_sweep_t<D3Q19, float>(odd, a32, st);
-    case 2: return launch_sweep_t<D3Q19, __nv_bfloat16>(odd, a32, st);
-    case 3: return launch_sweep_t<D3Q19, __half>(odd, a32, st);
+    case 0: return launch_sweep_t<D3Q19, double>(odd, a64, tiles, n_tiles, bx, st);
+    case 1: return launch_sweep_t<D3Q19, float>(odd, a32, tiles, n_tiles, bx, st);
+    case 2: return launch_sweep_t<D3Q19, __nv_bfloat16>(odd, a32, tiles, n_tiles, bx, st);
+    case 3: return launch_sweep_t<D3Q19, __half>(odd, a32, tiles, n_tiles, bx, st);
     default: return cudaErrorInvalidValue;
   }
 }
