@@ -4,24 +4,13 @@
 //
 // All of them read populations through the AA layout of the sweep: after an even
 // number of steps f_i(x) sits in slot i of x, after an odd number in slot opp(i)
-// of x - e_i.  They compute in double whatever the storage type.
+// of x - e_i, or in the link buffer for a cut link.  They compute in double
+// whatever the storage type.
 #include "common.cuh"
 
 namespace lbm {
 
 namespace {
-
-template <class L>
-__device__ __forceinline__ long long slot(int i, long long n, bool odd, const AuxArgs &a) {
-  if (!odd) return (long long)i * a.S + n;
-  const int x = (int)(n % a.nx);
-  const long long r = n / a.nx;
-  const int y = (int)(r % a.ny);
-  const int z = (int)(r / a.ny);
-  const long long nb =
-      wrap_index(x, y, z, -L::ex(i), -L::ey(i), -L::ez(i), a.nx, a.ny, a.nz, a.sy, a.sz);
-  return (long long)L::opp(i) * a.S + nb;
-}
 
 __device__ __forceinline__ double quiet_nan() { return __longlong_as_double(0x7ff8000000000000LL); }
 
@@ -61,7 +50,7 @@ __global__ void get_pop_kernel(AuxArgs a, bool odd, double *f) {
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
       double v = quiet_nan();
-      if (!solid) v = L::w(i) * a.rho0 + (double)Storage<T>::load(pop + slot<L>(i, n, odd, a));
+      if (!solid) v = L::w(i) * a.rho0 + (double)Storage<T>::load(population_address<L, T>(i, n, odd, a));
       f[(long long)i * a.N + n] = v;
     }
   }
@@ -89,7 +78,7 @@ __device__ __forceinline__ void node_moments(const AuxArgs &a, const T *pop, lon
   j[0] = j[1] = j[2] = 0;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
-    const double g = (double)Storage<T>::load(pop + slot<L>(i, n, odd, a));
+    const double g = (double)Storage<T>::load(population_address<L, T>(i, n, odd, a));
     drho += g;
     j[0] += L::ex(i) * g;
     j[1] += L::ey(i) * g;

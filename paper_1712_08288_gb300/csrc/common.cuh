@@ -65,6 +65,28 @@ __device__ __forceinline__ long long wrap_index(int x, int y, int z, int dx, int
   return xs + (long long)nx * (ys + (long long)ny * zs);
 }
 
+// Address of f_i(x_n, t) in the AA layout: after an even number of steps slot i of
+// x_n; after an odd number slot opp(i) of x_n - e_i, except for a cut link
+// (x_n - e_i solid), whose value sits in the link buffer.
+template <class L, class T>
+__device__ __forceinline__ const T *population_address(int i, long long n, bool odd,
+                                                       const AuxArgs &a) {
+  const T *pop = static_cast<const T *>(a.pop);
+  if (!odd) return pop + (long long)i * a.S + n;
+  const int d = L::opp(i);
+  if (d != i && a.cls[n] == kBoundary) {
+    const int b = a.bidx[n];
+    const uint32_t m = a.bmask[b];
+    if ((m >> d) & 1u)
+      return static_cast<const T *>(a.lnk) + a.boff[b] + __popc(m & ((1u << d) - 1u));
+  }
+  const int x = (int)(n % a.nx);
+  const long long r = n / a.nx;
+  const int y = (int)(r % a.ny), z = (int)(r / a.ny);
+  return pop + (long long)d * a.S +
+         wrap_index(x, y, z, -L::ex(i), -L::ey(i), -L::ez(i), a.nx, a.ny, a.nz, a.sy, a.sz);
+}
+
 // dispatch helper: storage type for an lbm_precision value
 template <class F>
 __host__ inline cudaError_t with_storage(int precision, F &&f) {

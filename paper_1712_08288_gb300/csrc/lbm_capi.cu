@@ -19,13 +19,13 @@
 
 namespace lbm {
 cudaError_t launch_sweep_d2q9(int, bool, const SweepArgs<double> &, const SweepArgs<float> &,
-                              const int4 *, int, int, cudaStream_t);
+                              const TileDesc *, int, int, cudaStream_t);
 cudaError_t launch_sweep_d3q19(int, bool, const SweepArgs<double> &, const SweepArgs<float> &,
-                               const int4 *, int, int, cudaStream_t);
+                               const TileDesc *, int, int, cudaStream_t);
 int error_norms_noalloc(int device, int lattice, int precision, const AuxArgs &a, bool odd,
                         const double *u_ref, double *out, cudaStream_t st, const char **why);
 cudaError_t launch_sweep(int lattice, int precision, bool odd, const SweepArgs<double> &a64,
-                         const SweepArgs<float> &a32, const int4 *tiles, int n_tiles, int bx,
+                         const SweepArgs<float> &a32, const TileDesc *tiles, int n_tiles, int bx,
                          cudaStream_t st) {
   return lattice == LBM_D2Q9 ? launch_sweep_d2q9(precision, odd, a64, a32, tiles, n_tiles, bx, st)
                              : launch_sweep_d3q19(precision, odd, a64, a32, tiles, n_tiles, bx, st);
@@ -55,7 +55,9 @@ struct lbm_ctx {
   int32_t *bidx = nullptr;
   uint32_t *bmask = nullptr;
   int32_t *boff = nullptr;
+  uint32_t *rec32 = nullptr;    // packed records of boundary nodes
   void *coef = nullptr;
+  void *lnk = nullptr;          // boundary values carried from an even to an odd step
   int *status = nullptr;
   double *partials = nullptr;   // norm reduction scratch
   double *norm_out = nullptr;
@@ -63,7 +65,7 @@ struct lbm_ctx {
   double *u_prev = nullptr;
   double *mom_rho = nullptr;
   double *mom_u = nullptr;
-  int4 *tiles = nullptr;        // active tiles of the sweep
+  TileDesc *tiles = nullptr;    // active tiles of the sweep
   int n_tiles = 0;
   int bx = 128;                 // tile width = threads per block
 
@@ -103,6 +105,9 @@ static int store_bytes(int precision) {
   return precision == LBM_F64 ? 8 : (precision == LBM_F32_DEV ? 4 : 2);
 }
 
+// guard bytes after the node-class and record arrays (aligned window copies)
+constexpr size_t kGuardBytes = 1024;
+
 static size_t pop_alloc_bytes(const lbm_ctx *c) {
   return (size_t)c->Q * slot_stride(c->N) * store_bytes(c->precision) + 2 * kPopPadBytes;
 }
@@ -128,6 +133,10 @@ static AuxArgs aux_args(const lbm_ctx *c) {
   a.S = slot_stride(c->N);
   a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.sy = c->sy; a.sz = c->sz;
   a.cls = c->cls;
+  a.bidx = c->bidx;
+  a.bmask = c->bmask;
+  a.boff = c->boff;
+  a.lnk = c->lnk;
   a.rho0 = c->rho0;
   for (int k = 0; k < 3; ++k) a.g[k] = c->g[k];
   return a;
@@ -136,7 +145,9 @@ static AuxArgs aux_args(const lbm_ctx *c) {
 static void refresh_args(lbm_ctx *c) {
   DevGeometry geo;
   geo.cls = c->cls; geo.bidx = c->bidx; geo.bmask = c->bmask; geo.boff = c->boff;
+  geo.rec32 = c->rec32;
   geo.coef = c->coef;
+  geo.lnk = c->lnk;
   auto fill = [&](auto &a) {
     using C = std::remove_reference_t<decltype(a.inv_rho0)>;
     a.pop = c->pop;
@@ -223,30 +234,62 @@ static void free_geometry(lbm_ctx *c) {
   cudaFree(c->bmask); c->bmask = nullptr;
   cudaFree(c->boff); c->boff = nullptr;
   cudaFree(c->coef); c->coef = nullptr;
+  cudaFree(c->lnk); c->lnk = nullptr;
 }
 
-// Tiles (x0, y, z) of bx consecutive nodes along x that hold at least one fluid
-// node; solid-only runs are never launched.  solid == nullptr: all fluid.
-static int upload_tiles(lbm_ctx *c, const uint8_t *solid) {
-  c->bx = 32;   // one warp per tile
+// Tile descriptors (see TileDesc) of every run of kTileW nodes along x that holds
+// at least one fluid node, and the packed records of the boundary nodes, in node
+// order.  solid == nullptr: an all-fluid box without cut links.
+static int upload_tiles(lbm_ctx *c, const uint8_t *solid, const std::vector<uint8_t> *cls,
+                        const std::vector<uint32_t> *bmask, const std::vector<int32_t> *boff) {
+  if (c->ny > 65535 || c->nz > 65535)
+    return fail(c, LBM_EINVAL, "grid: ny and nz must be below 65536");
+  c->bx = kTileW;   // one warp per tile
   const int nxb = (c->nx + c->bx - 1) / c->bx;
-  std::vector<int4> t;
+  std::vector<TileDesc> t;
   t.reserve((size_t)nxb * c->ny * c->nz);
+  std::vector<uint32_t> rec32;
+  if (bmask) rec32.reserve(bmask->size());
+  int rb = 0;
   for (int z = 0; z < c->nz; ++z)
     for (int y = 0; y < c->ny; ++y)
       for (int xb = 0; xb < nxb; ++xb) {
-        const int x0 = xb * c->bx, x1 = std::min(c->nx, x0 + c->bx);
-        bool any = solid == nullptr;
+        const int x0 = xb * c->bx;
         const long long row = (long long)c->nx * (y + (long long)c->ny * z);
-        for (int x = x0; x < x1 && !any; ++x) any = solid[row + x] == 0;
-        if (any) t.push_back(make_int4(x0, y, z, 0));
+        TileDesc d{};
+        d.x0 = x0;
+        d.yz = y | (z << 16);
+        d.rb = rb;
+        d.lb = 0;
+        bool any = false;
+        for (int k = 0; k < kTileW; ++k) {
+          const int x = x0 + k;
+          const bool is_solid = x >= c->nx || (solid && solid[row + x]);
+          if (is_solid) { d.solid |= 1ull << k; continue; }
+          any = true;
+          if (cls && (*cls)[row + x] == kBoundary) {
+            const uint32_t m = (*bmask)[rb], off = (uint32_t)(*boff)[rb];
+            if (!d.bnd) d.lb = (int)off;
+            d.bnd |= 1ull << k;
+            rec32.push_back(m | ((off - (uint32_t)d.lb) << kRecShift));
+            ++rb;
+          }
+        }
+        if (any) t.push_back(d);
       }
+  c->n_tiles = (int)t.size();
   cudaFree(c->tiles);
   c->tiles = nullptr;
-  c->n_tiles = (int)t.size();
-  if (t.empty()) return LBM_OK;
-  CUDA_OR_FAIL(c, cudaMalloc((void **)&c->tiles, sizeof(int4) * t.size()));
-  CUDA_OR_FAIL(c, cudaMemcpy(c->tiles, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice));
+  cudaFree(c->rec32);
+  c->rec32 = nullptr;
+  CUDA_OR_FAIL(c, cudaMalloc((void **)&c->tiles, sizeof(TileDesc) * std::max<size_t>(1, t.size())));
+  if (!t.empty())
+    CUDA_OR_FAIL(c, cudaMemcpy(c->tiles, t.data(), sizeof(TileDesc) * t.size(), cudaMemcpyHostToDevice));
+  CUDA_OR_FAIL(c, cudaMalloc((void **)&c->rec32, sizeof(uint32_t) * rec32.size() + kGuardBytes));
+  CUDA_OR_FAIL(c, cudaMemset(c->rec32, 0, sizeof(uint32_t) * rec32.size() + kGuardBytes));
+  if (!rec32.empty())
+    CUDA_OR_FAIL(c, cudaMemcpy(c->rec32, rec32.data(), sizeof(uint32_t) * rec32.size(),
+                               cudaMemcpyHostToDevice));
   return LBM_OK;
 }
 
@@ -285,10 +328,10 @@ int lbm_create(lbm_ctx **out, int lattice, int nx, int ny, int nz, const double 
   const size_t pop_bytes = pop_alloc_bytes(c);
   if (e == cudaSuccess) e = cudaMalloc(&c->pop_alloc, pop_bytes);
   if (e == cudaSuccess) c->pop = static_cast<char *>(c->pop_alloc) + kPopPadBytes;
-  if (e == cudaSuccess) e = cudaMalloc((void **)&c->cls, N);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->cls, N + kGuardBytes);
   if (e == cudaSuccess) e = cudaMalloc((void **)&c->status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->pop_alloc, 0, pop_bytes);
-  if (e == cudaSuccess) e = cudaMemset(c->cls, kFluid, N);
+  if (e == cudaSuccess) e = cudaMemset(c->cls, kFluid, N + kGuardBytes);
   if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int));
   if (e != cudaSuccess) {
     int code = e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
@@ -298,7 +341,7 @@ int lbm_create(lbm_ctx **out, int lattice, int nx, int ny, int nz, const double 
   }
   c->n_fluid = N;
   c->geometry_set = true;  // all-fluid periodic box, no links
-  if (upload_tiles(c, nullptr) != LBM_OK) {
+  if (upload_tiles(c, nullptr, nullptr, nullptr, nullptr) != LBM_OK) {
     g_create_error = c->err;
     lbm_destroy(c);
     return LBM_ECUDA;
@@ -316,13 +359,16 @@ int lbm_destroy(lbm_ctx *c) {
   cudaFree(c->cls);
   cudaFree(c->status);
   free_geometry(c);
+  cudaFree(c->tiles);
+  c->tiles = nullptr;
+  cudaFree(c->rec32);
+  c->rec32 = nullptr;
   cudaFree(c->partials);
   cudaFree(c->norm_out);
   cudaFree(c->u_ref);
   cudaFree(c->u_prev);
   cudaFree(c->mom_rho);
   cudaFree(c->mom_u);
-  cudaFree(c->tiles);
   delete c;
   return LBM_OK;
 }
@@ -459,6 +505,8 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *solid, int64_t n_links, const in
   CUDA_OR_FAIL(c, cudaMalloc((void **)&c->bmask, sizeof(uint32_t) * nb));
   CUDA_OR_FAIL(c, cudaMalloc((void **)&c->boff, sizeof(int32_t) * nb));
   CUDA_OR_FAIL(c, cudaMalloc(&c->coef, 4 * cb * std::max<long long>(1, n_links)));
+  CUDA_OR_FAIL(c, cudaMalloc(&c->lnk, (size_t)store_bytes(c->precision) * std::max<long long>(1, n_links)));
+  CUDA_OR_FAIL(c, cudaMemset(c->lnk, 0, (size_t)store_bytes(c->precision) * std::max<long long>(1, n_links)));
   if (!bmask.empty()) {
     CUDA_OR_FAIL(c, cudaMemcpy(c->bmask, bmask.data(), sizeof(uint32_t) * bmask.size(),
                                cudaMemcpyHostToDevice));
@@ -466,7 +514,7 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *solid, int64_t n_links, const in
                                cudaMemcpyHostToDevice));
   }
   if ((rc = upload_coefficients(c)) != LBM_OK) return rc;
-  if ((rc = upload_tiles(c, solid)) != LBM_OK) return rc;
+  if ((rc = upload_tiles(c, solid, &cls, &bmask, &boff)) != LBM_OK) return rc;
   CUDA_OR_FAIL(c, cudaMemset(c->pop_alloc, 0, pop_alloc_bytes(c)));
   CUDA_OR_FAIL(c, cudaMemset(c->status, 0, sizeof(int)));
   cudaFree(c->u_prev);

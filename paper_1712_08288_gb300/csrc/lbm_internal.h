@@ -9,20 +9,52 @@
 
 namespace lbm {
 
+// Tile width of the sweep: a warp handles kTileW consecutive nodes along x,
+// kNodesPerLane per lane.
+#ifndef LBM_NPL
+#define LBM_NPL 2
+#endif
+constexpr int kNodesPerLane = LBM_NPL;
+constexpr int kTileW = 32 * kNodesPerLane;
+
+static_assert(kTileW <= 64, "tile lane masks are 64-bit");
+
+// One unit of sweep work: kTileW consecutive nodes (x0 .. x0+kTileW-1) of row
+// (y, z) = (yz & 0xffff, yz >> 16) holding at least one fluid node.  Bit k of
+// solid is set when node x0+k is solid or lies beyond the row; bit k of bnd when
+// it is a boundary node.  The tile's boundary records are rec32[rb ...] in node
+// order, and its cut links start at link lb.
+struct alignas(16) TileDesc {
+  int x0, yz, rb, lb;
+  unsigned long long solid, bnd;
+};
+// packed record of a boundary node: cut-direction mask in bits 0..18, offset of
+// its first link relative to the tile's lb in bits 19..31
+constexpr int kRecShift = 19;
+
 // node classes stored one byte per node
 enum : uint8_t { kFluid = 0, kBoundary = 1, kSolid = 2 };
 
 // Geometry on the device.  Boundary nodes (fluid nodes with at least one cut link)
 // own a record b = bidx[n]: bmask[b] has bit d set when x_n + e_d is solid, and the
 // node's links occupy coef[boff[b] .. boff[b] + popcount(bmask[b]) - 1] in
-// ascending d.
+// ascending d.  rec32[b] holds the same record packed relative to its tile, for
+// the sweep's bulk copies; records are numbered in node order, so the records of
+// one tile are contiguous.  rec32 is allocated with guard bytes after its end.
 struct DevGeometry {
   const uint8_t *cls = nullptr;
   const int32_t *bidx = nullptr;
   const uint32_t *bmask = nullptr;
   const int32_t *boff = nullptr;
+  const uint32_t *rec32 = nullptr; // packed records (see TileDesc), in node order
   const void *coef = nullptr;      // 4 coefficients per link, compute type
+  void *lnk = nullptr;             // one storage element per link (see below)
 };
+
+// The link buffer carries, from an even step to the following odd step, the value
+// f_i(x_f, t+1) the boundary scheme produced for each cut link (i = opp(d)).  The
+// odd step reads it where the plain AA pattern would read slot d of the solid
+// neighbour x_f + e_d, so solid nodes' slots are never written or needed.
 
 // Per-link coefficients of Eq. 2.13 with b folded in: the new value of the
 // population i = opp(d) is (1-b) g_i + a g_d + bb g'_i + c g'_d + w.
@@ -57,9 +89,8 @@ struct SweepArgs {
 };
 
 // launchers (return cudaGetLastError() of the launch)
-// tiles: n_tiles runs (x0, y, z) of bx nodes along x holding at least one fluid node
 cudaError_t launch_sweep(int lattice, int precision, bool odd, const SweepArgs<double> &a64,
-                         const SweepArgs<float> &a32, const int4 *tiles, int n_tiles, int bx,
+                         const SweepArgs<float> &a32, const TileDesc *tiles, int n_tiles, int bx,
                          cudaStream_t st);
 
 struct AuxArgs {
@@ -68,6 +99,10 @@ struct AuxArgs {
   long long S;               // slot stride
   int nx, ny, nz, sy, sz;
   const uint8_t *cls;
+  const int32_t *bidx;       // boundary records and link buffer (odd-time reads)
+  const uint32_t *bmask;
+  const int32_t *boff;
+  const void *lnk;
   double rho0;
   double g[3];
 };

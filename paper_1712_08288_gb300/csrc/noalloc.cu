@@ -35,7 +35,6 @@ static __device__ __align__(256) double g_noalloc_partials[kNoAllocBlocks * kFie
 template <class L, class T>
 __global__ void __launch_bounds__(kNoAllocThreads)
     noalloc_partials_kernel(AuxArgs a, bool odd, const double *u_ref, double *partials) {
-  const T *pop = static_cast<const T *>(a.pop);
   double acc[kFields];
 #pragma unroll
   for (int k = 0; k < kFields; ++k) acc[k] = 0.0;
@@ -44,17 +43,10 @@ __global__ void __launch_bounds__(kNoAllocThreads)
   if (end > a.N) end = a.N;
   for (long long n = begin + threadIdx.x; n < end; n += kNoAllocThreads) {
     if (a.cls[n] == kSolid) continue;
-    const int x = (int)(n % a.nx);
-    const long long r = n / a.nx;
-    const int y = (int)(r % a.ny), z = (int)(r / a.ny);
     double drho = 0.0, j[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-      long long s = (long long)i * a.S + n;                 // even time: own slot i
-      if (odd)                                              // odd time: slot opp(i) of x - e_i
-        s = (long long)L::opp(i) * a.S +
-            wrap_index(x, y, z, -L::ex(i), -L::ey(i), -L::ez(i), a.nx, a.ny, a.nz, a.sy, a.sz);
-      const double g = (double)Storage<T>::load(pop + s);
+      const double g = (double)Storage<T>::load(population_address<L, T>(i, n, odd, a));
       drho += g;
       j[0] += L::ex(i) * g;
       j[1] += L::ey(i) * g;

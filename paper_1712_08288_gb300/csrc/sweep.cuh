@@ -12,11 +12,11 @@
 // x_f + e_d is solid, the population i = opp(d) that would arrive from that
 // neighbour is produced by the single-node scheme, Eqs. 2.10 and 2.13, from the
 // node's own pre-collision f_i, f_d and post-collision f'_i, f'_d, which all sit in
-// registers at that point.  The value is written where the next step looks for
-// f_i(x_f, t+1): after an even step that is slot d of the solid neighbour
-// x_f + e_d (a ghost slot no other node writes), after an odd step slot i of x_f
-// itself (which only the solid node would otherwise write).  So the boundary
-// costs no extra population traffic.
+// registers at that point.  The value goes where the next step looks for
+// f_i(x_f, t+1): after an odd step into slot i of x_f itself (which only the solid
+// node would otherwise write); after an even step into the link's entry of a
+// compact link buffer, which the next odd step reads in place of slot d of the
+// solid neighbour.  Solid nodes' slots are never written.
 //
 // Collision (Appendix, MRT): in deviation variables g = f - w rho0,
 //   m = M g, m'_k = m_k - s_k (m_k - m^eq_k) for the non-conserved rows,
@@ -217,6 +217,9 @@ struct Neighbours {
 // Bulk-copy pipeline helpers (inline PTX, sm_90+): mbarrier with transaction
 // count, cp.async.bulk global -> shared.
 // ---------------------------------------------------------------------------
+constexpr uint32_t kSuspendHintNs = 1000000;   // 1 ms upper bound per poll
+constexpr int kWaitLimit = 1000;
+
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -229,18 +232,20 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                "r"(bytes)
                : "memory");
 }
+// try_wait with a suspend-time hint: a thread whose phase has not completed sleeps
+// (up to the hint) instead of spinning, so waiting warps do not take issue slots
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   uint32_t done;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(done)
-      : "r"(smem_addr(bar)), "r"(parity)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendHintNs)
       : "memory");
   return done != 0;
 }
-// bounded wait: false after kWaitLimit polls (each poll may suspend briefly)
-constexpr int kWaitLimit = 1 << 20;
+// bounded wait: gives up after kWaitLimit polls, i.e. after about
+// kWaitLimit * kSuspendHintNs = 1 s, far beyond any legitimate copy latency
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
   for (int it = 0; it < kWaitLimit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
@@ -255,13 +260,13 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
       : "memory");
 }
 
-// Work decomposition.  A tile is a run of kTileW = 32 nodes along x that holds at
-// least one fluid node; tiles are listed once per geometry.  Every warp owns a
+// Work decomposition.  A tile is a run of kTileW nodes along x that holds at
+// least one fluid node; tiles are listed once per geometry.  A warp processes a
+// tile kNodesPerLane nodes per lane, one node after the other.  Every warp owns a
 // private pipeline of kStages shared-memory stages: stage s holds the Q population
 // row windows of one tile (each window up to kTileW + 16/sizeof(T) elements, start
 // aligned down to 16 bytes), filled by bulk copies that complete on the warp's own
 // mbarrier.  Warps never wait for each other.
-constexpr int kTileW = 32;
 constexpr int kWarpsPerBlock = 4;
 
 #ifndef LBM_STAGES_4B
@@ -271,64 +276,102 @@ template <class T>
 struct StageShape {
   static constexpr int kStages = sizeof(T) == 8 ? 2 : (sizeof(T) == 4 ? LBM_STAGES_4B : 3);
   static constexpr int kWidth = kTileW + 16 / (int)sizeof(T);   // elements per window
+  static constexpr int kRecs = kTileW + 4;                       // record window (uint32)
 };
 
-// bytes of one warp's pipeline (stages, barriers, offsets), a multiple of 128 so
-// that every warp's stages start 128-byte aligned
+// Byte layout of one stage: Q population windows, then the record window; after
+// all stages, the barriers and the offsets (Q + 1 per stage).
+template <class L, class T>
+struct StageLayout {
+  using SS = StageShape<T>;
+  static constexpr size_t kPop = (size_t)L::Q * SS::kWidth * sizeof(T);
+  static constexpr size_t kRec = kPop;
+  static constexpr size_t kStage = (kRec + SS::kRecs * sizeof(uint32_t) + 15) / 16 * 16;
+  static constexpr size_t kBars = SS::kStages * kStage;
+  static constexpr size_t kOffs = kBars + SS::kStages * sizeof(uint64_t);
+  static constexpr int kNOff = L::Q + 1;
+};
+
+// bytes of one warp's pipeline, a multiple of 128 so that every warp's stages
+// start 128-byte aligned
 template <class L, class T>
 __host__ __device__ constexpr size_t warp_smem_bytes() {
-  return ((size_t)StageShape<T>::kStages * L::Q * StageShape<T>::kWidth * sizeof(T) +
-          StageShape<T>::kStages * (sizeof(uint64_t) + L::Q * sizeof(int)) + 127) / 128 * 128;
+  using SL = StageLayout<L, T>;
+  return (SL::kOffs + StageShape<T>::kStages * SL::kNOff * sizeof(int) + 127) / 128 * 128;
 }
 static_assert(warp_smem_bytes<D3Q19, float>() % 128 == 0, "warp region alignment");
+static_assert(StageLayout<D3Q19, float>::kRec % 16 == 0 && StageLayout<D3Q19, double>::kRec % 16 == 0 &&
+                  StageLayout<D3Q19, __half>::kRec % 16 == 0 && StageLayout<D2Q9, __half>::kRec % 16 == 0,
+              "record window alignment");
 static_assert((StageShape<float>::kWidth * sizeof(float)) % 16 == 0, "window stride");
 static_assert((StageShape<double>::kWidth * sizeof(double)) % 16 == 0, "window stride");
 static_assert((StageShape<__half>::kWidth * sizeof(__half)) % 16 == 0, "window stride");
 
-// Lanes 0..Q-1 of a warp fill one stage with the row windows of a tile, lane i
-// copying population i: in an even step the window [x0, x0+32) of slot i in the
-// tile's own row; in an odd step [x0 - ex_i, x0 - ex_i + 32) of slot opp(i) in row
-// (y - ey_i, z - ez_i).  Each copy starts at the 16-byte boundary at or before the
-// first element and covers the window rounded up to 16 bytes; off[i] records where
-// the tile's first element landed.  The offsets are stored before lane 0's arrive
-// (release), so a lane that has waited on the barrier sees them.  All 32 lanes call.
+// aligned-down source of a window and the element offset of its first element
+template <class E>
+__device__ __forceinline__ const char *align16(const E *p, int &off_elems) {
+  const char *pc = reinterpret_cast<const char *>(p);
+  const char *pa = reinterpret_cast<const char *>(reinterpret_cast<uintptr_t>(pc) & ~(uintptr_t)15);
+  off_elems = (int)((pc - pa) / (long long)sizeof(E));
+  return pa;
+}
+
+// One warp fills one stage with everything a tile needs, lane i issuing copy i:
+// lanes 0..Q-1 the population row windows (even step: window [x0, x0+kTileW) of slot
+// i in the tile's own row; odd step: [x0 - ex_i, x0 - ex_i + kTileW) of slot opp(i)
+// in row (y - ey_i, z - ez_i)), lane Q the tile's packed boundary records.  Every
+// copy starts at the 16-byte boundary at or before its first element and covers its
+// window rounded up to 16 bytes; off[] records where each first element landed.
+// The offsets are stored before lane 0's arrive (release), so a lane that has
+// waited on the barrier sees them.  All lanes call.
 template <class L, class T, bool ODD, class I>
-__device__ __forceinline__ void issue_tile(const SweepArgs<typename Storage<T>::C> &a, int4 tl,
-                                           T *stage, int *off, uint64_t *bar) {
+__device__ __forceinline__ void issue_tile(const SweepArgs<typename Storage<T>::C> &a,
+                                           const TileDesc &td, unsigned char *stage, int *off,
+                                           uint64_t *bar) {
+  using SL = StageLayout<L, T>;
   constexpr int W = StageShape<T>::kWidth;
   const int lane = threadIdx.x & 31;
-  const char *pa = nullptr;
+  const int ty = td.yz & 0xffff, tz = td.yz >> 16;
+  const char *src = nullptr;
+  void *dst = nullptr;
   uint32_t bytes = 0;
   if (lane < L::Q) {
     const int i = lane;
-    int slot = i, yy = tl.y, zz = tl.z, xs = tl.x;
+    int slot = i, yy = ty, zz = tz, xs = td.x0;
     if (ODD) {
       slot = L::opp_rt(i);
-      yy = wrap1(tl.y - DirBits<L>::ey(i), a.ny);
-      zz = (L::D == 3) ? wrap1(tl.z - DirBits<L>::ez(i), a.nz) : 0;
-      xs = tl.x - DirBits<L>::ex(i);
+      yy = wrap1(ty - DirBits<L>::ey(i), a.ny);
+      zz = (L::D == 3) ? wrap1(tz - DirBits<L>::ez(i), a.nz) : 0;
+      xs = td.x0 - DirBits<L>::ex(i);
     }
     const I elem = (I)slot * (I)a.S + (I)a.nx * ((I)yy + (I)a.ny * zz) + xs;
-    const char *p = static_cast<const char *>(a.pop) + (long long)elem * (long long)sizeof(T);
-    pa = reinterpret_cast<const char *>(reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)15);
-    const int delta = (int)((p - pa) / (long long)sizeof(T));
-    off[i] = delta;
-    bytes = ((uint32_t)((delta + kTileW) * (int)sizeof(T)) + 15u) & ~15u;
+    int o;
+    src = align16(static_cast<const T *>(a.pop) + elem, o);
+    off[i] = o;
+    bytes = ((uint32_t)((o + kTileW) * (int)sizeof(T)) + 15u) & ~15u;
+    dst = stage + (size_t)i * W * sizeof(T);
+  } else if (lane == L::Q) {
+    const int nrec = __popcll(td.bnd);
+    int o;
+    src = align16(a.geo.rec32 + td.rb, o);
+    off[L::Q] = o;
+    bytes = nrec > 0 ? (((uint32_t)((o + nrec) * (int)sizeof(uint32_t)) + 15u) & ~15u) : 0u;
+    dst = stage + SL::kRec;
   }
   const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
   __syncwarp();
   if (lane == 0) mbar_arrive_expect_tx(bar, total);
   __syncwarp();
-  if (lane < L::Q) bulk_copy_g2s(stage + lane * W, pa, bytes, bar);
+  if (bytes) bulk_copy_g2s(dst, src, bytes, bar);
 }
 
 // resident blocks per SM the register budget is sized for
 #ifndef LBM_MINBLOCKS_F32
-#define LBM_MINBLOCKS_F32 8
+#define LBM_MINBLOCKS_F32 5
 #endif
 template <class T>
 struct MinBlocks {
-  static constexpr int value = LBM_MINBLOCKS_F32;   // 8 x 128 threads: 64 registers
+  static constexpr int value = LBM_MINBLOCKS_F32;   // 5 x 128 threads: up to 96 registers
 };
 template <>
 struct MinBlocks<double> {
@@ -349,18 +392,19 @@ __device__ __forceinline__ constexpr int aligned_window_offset(int ex) {
 
 template <class L, class T, bool ODD, bool SKEW, bool ALIGNED, class I>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
-    sweep_kernel(const SweepArgs<typename Storage<T>::C> a, const int4 *__restrict__ tiles,
+    sweep_kernel(const SweepArgs<typename Storage<T>::C> a, const TileDesc *__restrict__ tiles,
                  int n_tiles) {
   using C = typename Storage<T>::C;
+  using SL = StageLayout<L, T>;
   constexpr int Q = L::Q;
   constexpr int NS = StageShape<T>::kStages;
   constexpr int W = StageShape<T>::kWidth;
+  constexpr int NO = SL::kNOff;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char *wsm = smem_raw + (size_t)warp * warp_smem_bytes<L, T>();
-  T *stages = reinterpret_cast<T *>(wsm);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + (size_t)NS * Q * W * sizeof(T));
-  int *offs = reinterpret_cast<int *>(bars + NS);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + SL::kBars);
+  int *offs = reinterpret_cast<int *>(wsm + SL::kOffs);
 
   const int gw = blockIdx.x * kWarpsPerBlock + warp;
   const int nw = gridDim.x * kWarpsPerBlock;
@@ -371,12 +415,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
   __syncwarp();
   for (int s = 0; s < NS; ++s) {
     const int tile = gw + s * nw;
-    if (tile < n_tiles) issue_tile<L, T, ODD, I>(a, tiles[tile], stages + s * Q * W, offs + s * Q, &bars[s]);
+    if (tile < n_tiles)
+      issue_tile<L, T, ODD, I>(a, tiles[tile], wsm + s * SL::kStage, offs + s * NO, &bars[s]);
   }
-  const int nxm1 = a.nx - 1;
 
   T *__restrict__ pop = static_cast<T *>(a.pop);
   const I S = (I)a.S;
+  const int nxm1 = a.nx - 1;
+  const LinkCoef<C> *coef = static_cast<const LinkCoef<C> *>(a.geo.coef);
+  T *const lnk = static_cast<T *>(a.geo.lnk);
   int k = 0;
   for (int tile = gw; tile < n_tiles; tile += nw, ++k) {
     const int s = k % NS;
@@ -388,25 +435,39 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
         if (tile + j * nw < n_tiles) mbar_wait_bounded(&bars[(k + j) % NS], (uint32_t)((k + j) / NS) & 1u);
       return;
     }
-    const int4 tl = tiles[tile];
-    const int x = tl.x + lane;
-    const int y = tl.y, z = tl.z;
-    const bool in_row = x < a.nx;
-    const int n = in_row ? x + a.nx * (y + a.ny * z) : 0;
-    const uint8_t cls = in_row ? __ldg(a.geo.cls + n) : (uint8_t)kSolid;
-    const T *st = stages + s * Q * W;
+    const TileDesc td = tiles[tile];
+    const int y = td.yz & 0xffff, z = td.yz >> 16;
+    const unsigned char *stg = wsm + s * SL::kStage;
+    const T *st = reinterpret_cast<const T *>(stg);
+    const uint32_t *rec_s = reinterpret_cast<const uint32_t *>(stg + SL::kRec) + offs[s * NO + Q];
+    const int row = a.nx * (y + a.ny * z);
+#pragma unroll 1
+    for (int j = 0; j < kNodesPerLane; ++j) {
+    const int xl = j * 32 + lane;          // position inside the tile
+    const int x = td.x0 + xl;
+    const int n = row + x;
+    const bool solid = (td.solid >> xl) & 1ull;
+    int boff = 0;
+    uint32_t bmask = 0u;
+    if ((td.bnd >> xl) & 1ull) {
+      const uint32_t r = rec_s[__popcll(td.bnd & ((1ull << xl) - 1ull))];
+      bmask = r & ((1u << kRecShift) - 1u);
+      boff = td.lb + (int)(r >> kRecShift);
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(coef + boff));
+    }
     C g[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const int o = ALIGNED ? (ODD ? aligned_window_offset<T>(L::ex(i)) : 0) : offs[s * Q + i];
-      g[i] = Storage<T>::load(st + i * W + o + lane);
+      const int o = ALIGNED ? (ODD ? aligned_window_offset<T>(L::ex(i)) : 0) : offs[s * NO + i];
+      g[i] = Storage<T>::load(st + i * W + o + xl);
     }
-    __syncwarp();   // stage s consumed: refill it with the tile NS rounds ahead
-    {
+    if (j == kNodesPerLane - 1) {
+      __syncwarp();   // stage s consumed: refill it with the tile NS rounds ahead
       const int nt = tile + NS * nw;
-      if (nt < n_tiles) issue_tile<L, T, ODD, I>(a, tiles[nt], stages + s * Q * W, offs + s * Q, &bars[s]);
+      if (nt < n_tiles)
+        issue_tile<L, T, ODD, I>(a, tiles[nt], wsm + s * SL::kStage, offs + s * NO, &bars[s]);
     }
-    if (cls == kSolid) continue;
+    if (solid) continue;
 
     // lanes on the periodic x-edges: the row windows cannot follow the wrap
     const bool xlo = ODD && x == 0, xhi = ODD && x == nxm1;
@@ -420,6 +481,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
           g[i] = Storage<T>::load(pop + (I)L::opp(i) * S + (I)src);
         }
       }
+    }
+    if (ODD && bmask) {
+      // populations that arrive through a cut link were left in the link buffer
+      // by the previous (even) step
+#pragma unroll
+      for (int dd = 1; dd < Q; ++dd)
+        if (bmask & (1u << dd))
+          g[L::opp(dd)] = Storage<T>::load(lnk + boff + __popc(bmask & ((1u << dd) - 1u)));
     }
 
     C gp[Q];
@@ -454,72 +523,73 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
           }
         }
       } else {
-        const Neighbours<L, SKEW> nb(x, y, z, a.nx, a.ny, a.nz, a.sy, a.sz);
+        // rows of the tile touch a periodic edge in y or z: wrap every neighbour
 #pragma unroll
-        for (int i = 0; i < Q; ++i) Storage<T>::store(pop + (I)i * S + (I)nb(i), gp[i]);
+        for (int i = 0; i < Q; ++i) {
+          const long long dn = wrap_index(x, y, z, L::ex(i), L::ey(i), L::ez(i), a.nx, a.ny, a.nz,
+                                          a.sy, a.sz);
+          Storage<T>::store(pop + (I)i * S + (I)dn, gp[i]);
+        }
       }
     }
 
     // single-node boundary scheme on the cut links of this node (Eqs. 2.10, 2.13)
-    if (cls == kBoundary) {
-      const int b = __ldg(a.geo.bidx + n);
-      const uint32_t mask = __ldg(a.geo.bmask + b);
-      const int off = __ldg(a.geo.boff + b);
-      const LinkCoef<C> *coef = static_cast<const LinkCoef<C> *>(a.geo.coef);
+    if (bmask) {
 #pragma unroll
       for (int dd = 1; dd < Q; ++dd) {
-        if (mask & (1u << dd)) {
-          const LinkCoef<C> c = coef[off + __popc(mask & ((1u << dd) - 1u))];
+        if (bmask & (1u << dd)) {
+          const int kk = boff + __popc(bmask & ((1u << dd) - 1u));
+          const LinkCoef<C> c = coef[kk];
           const int i = L::opp(dd);
           const C v = a.one_minus_b * g[i] + c.a * g[dd] + c.bb * gp[i] + c.c * gp[dd] + c.w;
-          I dst;
-          if (!ODD) {
-            // slot dd of the solid neighbour x_f + e_dd (read there by the next odd step)
-            const long long sn = wrap_index(x, y, z, L::ex(dd), L::ey(dd), L::ez(dd), a.nx, a.ny,
-                                            a.nz, a.sy, a.sz);
-            dst = (I)dd * S + (I)sn;
-          } else {
-            dst = (I)i * S + (I)n;   // slot i of x_f itself (read there by the next even step)
-          }
-          Storage<T>::store(pop + dst, v);
+          if (!ODD) Storage<T>::store(lnk + kk, v);          // read by the next odd step
+          else Storage<T>::store(pn + (I)i * S, v);          // slot i of x_f itself
         }
       }
+    }
     }
   }
 }
 
-// persistent grid size per kernel instantiation: resident blocks per SM x SMs
-template <class K>
-int persistent_blocks(K kernel, int bx, size_t smem) {
+// Persistent grid size of one kernel instantiation (resident blocks per SM x
+// SMs), computed once per kernel; also raises the kernel's dynamic shared-memory
+// limit to what it uses.
+template <auto Kernel>
+int persistent_blocks(int threads, size_t smem) {
   static int cached = 0;
   if (cached == 0) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, bx, smem);
+    cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, Kernel, threads, smem);
     cached = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
   }
   return cached;
 }
 
+template <auto Kernel, class A>
+void launch_persistent(const A &a, const TileDesc *tiles, int n_tiles, size_t smem, cudaStream_t st) {
+  const int threads = kWarpsPerBlock * 32;
+  int grid = persistent_blocks<Kernel>(threads, smem);
+  const int need = (n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (grid > need) grid = need;
+  Kernel<<<grid, threads, smem, st>>>(a, tiles, n_tiles);
+}
+
 template <class L, class T>
-cudaError_t launch_sweep_t(bool odd, const SweepArgs<typename Storage<T>::C> &a, const int4 *tiles,
+cudaError_t launch_sweep_t(bool odd, const SweepArgs<typename Storage<T>::C> &a, const TileDesc *tiles,
                            int n_tiles, int bx, cudaStream_t st) {
   if (n_tiles == 0) return cudaSuccess;
   const bool skew = a.sy != 0 || a.sz != 0;
   const bool big = (long long)L::Q * a.S >= (1LL << 31);
   const size_t smem = kWarpsPerBlock * warp_smem_bytes<L, T>();
-  const int threads = kWarpsPerBlock * 32;
   (void)bx;
   const bool aligned = ((long long)a.nx * (long long)sizeof(T)) % 16 == 0;
-#define LBM_LAUNCH(O, S, I)                                                        \
-  do {                                                                             \
-    auto kern = aligned ? sweep_kernel<L, T, O, S, true, I> : sweep_kernel<L, T, O, S, false, I>; \
-    int grid = persistent_blocks(kern, threads, smem);                             \
-    const int need = (n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;              \
-    if (grid > need) grid = need;                                                  \
-    kern<<<grid, threads, smem, st>>>(a, tiles, n_tiles);                          \
+#define LBM_LAUNCH(O, S, I)                                                              \
+  do {                                                                                   \
+    if (aligned) launch_persistent<sweep_kernel<L, T, O, S, true, I>>(a, tiles, n_tiles, smem, st);   \
+    else launch_persistent<sweep_kernel<L, T, O, S, false, I>>(a, tiles, n_tiles, smem, st);         \
   } while (0)
   if (big) {
     if (odd) { if (skew) LBM_LAUNCH(true, true, long long); else LBM_LAUNCH(true, false, long long); }

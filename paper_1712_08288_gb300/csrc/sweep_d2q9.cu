@@ -5,7 +5,7 @@
 namespace lbm {
 
 cudaError_t launch_sweep_d2q9(int precision, bool odd, const SweepArgs<double> &a64,
-                           const SweepArgs<float> &a32, const int4 *tiles, int n_tiles,
+                           const SweepArgs<float> &a32, const TileDesc *tiles, int n_tiles,
                            int bx, cudaStream_t st) {
   switch (precision) {
     case 0: return launch_sweep_t<D2Q9, double>(odd, a64, tiles, n_tiles, bx, st);
