@@ -42,7 +42,7 @@ WORKLOAD = ("D3Q19 MRT body-force Poiseuille flow in a tilted periodic pipe, L=2
             "(16.8M nodes), R=0.4L, axis (16,4,3), skewed x-wrap, single-node scheme l=gamma b=1")
 SCHEME = (0.0, 1.0, 0.0, 1.0)
 BYTES = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}
-PROFILE = os.path.join(ROOT, "profiles", "sweep_d3q19_f32_pipe256.txt")
+PROFILE = os.path.join(ROOT, "profiles", "sweep_d3q19_f32_pipe192.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1712_08288_gb300", "csrc", f)
                   for f in ("sweep.cuh", "common.cuh", "lattice.h", "lbm_internal.h")]
 
