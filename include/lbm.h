@@ -186,6 +186,30 @@ int lbm_error_norms(lbm_ctx *ctx, const double *u_ref, lbm_norms *out);
  * that overlap on the GPU race on it, so issue them in order on one stream. */
 int lbm_error_norms_noalloc(lbm_ctx *ctx, const double *u_ref_dev, double *out_dev);
 
+/* Batches (ensembles of independent problems).  A batch advances several contexts
+ * -- same lattice, precision and device, any sizes, geometries and parameters --
+ * by ONE persistent sweep launch per time step that walks the tiles of all of them,
+ * replayed from a CUDA graph holding an even and an odd step.  Each context keeps
+ * its own state; stepping a batch is equivalent (bit for bit) to stepping every
+ * context alone.  Contexts are borrowed: they must outlive the batch, and they must
+ * be at the same time parity when the batch steps.  Changes to a member context
+ * (geometry, scheme, force) are picked up at the next batch call.
+ * lbm_batch_set_config: order of tiles in the launch (0 context after context,
+ * 1 round-robin over contexts, 2 largest context first) and resident blocks per SM
+ * (0 = as many as fit).  lbm_batch_tune times every (order, blocks) pair over
+ * trial_steps steps, keeps the fastest and restores the contexts' state, so tuning
+ * does not advance the simulations. */
+typedef struct lbm_batch lbm_batch;
+int lbm_batch_create(lbm_batch **out, int n, lbm_ctx *const *ctxs);
+int lbm_batch_destroy(lbm_batch *batch);
+int lbm_batch_set_stream(lbm_batch *batch, void *cuda_stream);
+int lbm_batch_set_config(lbm_batch *batch, int order, int blocks_per_sm);
+int lbm_batch_tune(lbm_batch *batch, int trial_steps, int *order, int *blocks_per_sm);
+int lbm_batch_step(lbm_batch *batch, int n);
+int lbm_batch_query(const lbm_batch *batch, int *n_contexts, int64_t *tiles, int *order,
+                    int *blocks_per_sm);
+const char *lbm_batch_last_error(const lbm_batch *batch);
+
 /* Sizes: lattice Q and D, node counts, link count. */
 int lbm_query(const lbm_ctx *ctx, int *Q, int *D, int64_t *nodes, int64_t *fluid_nodes,
               int64_t *links);

@@ -25,7 +25,9 @@ STATUS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA",
 EXPORTS = ["lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_set_skew", "lbm_set_geometry",
            "lbm_set_scheme", "lbm_set_force", "lbm_init_equilibrium", "lbm_set_populations",
            "lbm_get_populations", "lbm_step", "lbm_time", "lbm_moments", "lbm_moments_device",
-           "lbm_error_norms", "lbm_error_norms_noalloc", "lbm_query", "lbm_last_error"]
+           "lbm_error_norms", "lbm_error_norms_noalloc", "lbm_query", "lbm_last_error",
+           "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_set_stream", "lbm_batch_set_config",
+           "lbm_batch_tune", "lbm_batch_step", "lbm_batch_query", "lbm_batch_last_error"]
 
 
 class lbm_norms(ct.Structure):
@@ -57,6 +59,14 @@ def load_library(path=LIB_PATH):
         "lbm_error_norms_noalloc": (I, [P, P, P]),
         "lbm_query": (I, [P, P, P, P, P, P]),
         "lbm_last_error": (ct.c_char_p, [P]),
+        "lbm_batch_create": (I, [ct.POINTER(P), I, P]),
+        "lbm_batch_destroy": (I, [P]),
+        "lbm_batch_set_stream": (I, [P, P]),
+        "lbm_batch_set_config": (I, [P, I, I]),
+        "lbm_batch_tune": (I, [P, I, P, P]),
+        "lbm_batch_step": (I, [P, I]),
+        "lbm_batch_query": (I, [P, P, P, P, P]),
+        "lbm_batch_last_error": (ct.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -199,6 +209,56 @@ class Lbm:
         self._check(self._lib.lbm_query(self.h, ct.byref(Q), ct.byref(D), ct.byref(n), ct.byref(nf),
                                         ct.byref(nl)))
         return dict(Q=Q.value, D=D.value, nodes=n.value, fluid_nodes=nf.value, links=nl.value)
+
+
+class Batch:
+    """lbm_batch: several contexts advanced by one persistent launch per step."""
+
+    ORDERS = {0: "context-major", 1: "round-robin", 2: "largest-first"}
+
+    def __init__(self, sims):
+        self._lib = lib()
+        self.sims = list(sims)          # keep the contexts alive while the batch exists
+        arr = (ct.c_void_p * len(self.sims))(*[s.h.value for s in self.sims])
+        h = ct.c_void_p()
+        rc = self._lib.lbm_batch_create(ct.byref(h), len(self.sims), ct.cast(arr, ct.c_void_p))
+        if rc != 0:
+            raise LbmError(rc, self._lib.lbm_batch_last_error(None).decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc != 0:
+            raise LbmError(rc, self._lib.lbm_batch_last_error(self.h).decode())
+
+    def set_stream(self, stream_handle):
+        self._check(self._lib.lbm_batch_set_stream(self.h, ct.c_void_p(stream_handle)))
+
+    def set_config(self, order, blocks_per_sm=0):
+        self._check(self._lib.lbm_batch_set_config(self.h, int(order), int(blocks_per_sm)))
+
+    def tune(self, trial_steps=20):
+        o, b = ct.c_int(), ct.c_int()
+        self._check(self._lib.lbm_batch_tune(self.h, int(trial_steps), ct.byref(o), ct.byref(b)))
+        return o.value, b.value
+
+    def step(self, n=1):
+        self._check(self._lib.lbm_batch_step(self.h, int(n)))
+
+    def query(self):
+        n, t, o, b = ct.c_int(), ct.c_int64(), ct.c_int(), ct.c_int()
+        self._check(self._lib.lbm_batch_query(self.h, ct.byref(n), ct.byref(t), ct.byref(o), ct.byref(b)))
+        return dict(contexts=n.value, tiles=t.value, order=o.value, blocks_per_sm=b.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def from_workload(w, precision="f64", scheme=(0.0, 1.0, 0.0, 1.0), allow_nonconvex=False):

@@ -24,6 +24,10 @@ cudaError_t launch_sweep_d3q19(int, bool, const SweepArgs<double> &, const Sweep
                                const TileDesc *, int, int, cudaStream_t);
 int error_norms_noalloc(int device, int lattice, int precision, const AuxArgs &a, bool odd,
                         const double *u_ref, double *out, cudaStream_t st, const char **why);
+cudaError_t launch_sweep_batch_d2q9(int, bool, const void *, const TileDesc *, const int *, int,
+                                   bool, int, cudaStream_t, bool);
+cudaError_t launch_sweep_batch_d3q19(int, bool, const void *, const TileDesc *, const int *, int,
+                                    bool, int, cudaStream_t, bool);
 cudaError_t launch_sweep(int lattice, int precision, bool odd, const SweepArgs<double> &a64,
                          const SweepArgs<float> &a32, const TileDesc *tiles, int n_tiles, int bx,
                          cudaStream_t st) {
@@ -77,6 +81,7 @@ struct lbm_ctx {
 
   SweepArgs<double> a64;
   SweepArgs<float> a32;
+  long long version = 0;        // bumped whenever the sweep arguments change
   std::string err;
 };
 
@@ -180,6 +185,7 @@ static void refresh_args(lbm_ctx *c) {
   };
   fill(c->a64);
   fill(c->a32);
+  ++c->version;
 }
 
 // l(gamma) of the family (Sec. 2 / Sec. 3 rules)
@@ -719,6 +725,373 @@ int lbm_query(const lbm_ctx *c, int *Q, int *D, int64_t *nodes, int64_t *fluid_n
 
 const char *lbm_last_error(const lbm_ctx *c) {
   return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches: many contexts advanced by one persistent launch per step, replayed
+// from a CUDA graph.
+// ---------------------------------------------------------------------------
+struct lbm_batch {
+  std::vector<lbm_ctx *> ctx;
+  int lattice = 0, precision = 0, device = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<std::vector<TileDesc>> host_tiles;   // per context
+  std::vector<long long> versions;
+  void *inst = nullptr;          // SweepArgs per context (compute type of the precision)
+  TileDesc *tiles = nullptr;
+  int *tile_inst = nullptr;
+  int n_tiles = 0;
+  bool big = false;
+  int order = 1;                 // 0 context-major, 1 round-robin, 2 largest context first
+  int blocks_per_sm = 0;         // 0: as many as fit
+  cudaGraphExec_t graph = nullptr;
+  bool graph_odd = false;        // parity of the first launch in the graph
+  int graph_pairs = 0;           // even+odd launch pairs captured in the graph
+  std::string err;
+};
+
+static int bfail(lbm_batch *b, int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (b) b->err = buf;
+  else g_create_error = buf;
+  return code;
+}
+
+#define BCUDA(b, call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return bfail(b, e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s", \
+                   #call, cudaGetErrorString(e_));                                      \
+  } while (0)
+
+static void batch_drop_graph(lbm_batch *b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->graph_pairs = 0;
+}
+
+// merged tile list in the batch's order and the per-context argument table
+static int batch_upload(lbm_batch *b) {
+  const int n = (int)b->ctx.size();
+  std::vector<TileDesc> t;
+  std::vector<int> ti;
+  size_t total = 0;
+  for (auto &v : b->host_tiles) total += v.size();
+  t.reserve(total);
+  ti.reserve(total);
+  std::vector<int> ctx_order(n);
+  for (int k = 0; k < n; ++k) ctx_order[k] = k;
+  if (b->order == 2)
+    std::stable_sort(ctx_order.begin(), ctx_order.end(), [&](int p, int q) {
+      return b->host_tiles[p].size() > b->host_tiles[q].size();
+    });
+  if (b->order == 1) {
+    // round-robin: one tile of every context in turn
+    std::vector<size_t> pos(n, 0);
+    bool more = true;
+    while (more) {
+      more = false;
+      for (int k : ctx_order)
+        if (pos[k] < b->host_tiles[k].size()) {
+          t.push_back(b->host_tiles[k][pos[k]++]);
+          ti.push_back(k);
+          more = true;
+        }
+    }
+  } else {
+    for (int k : ctx_order)
+      for (const TileDesc &d : b->host_tiles[k]) {
+        t.push_back(d);
+        ti.push_back(k);
+      }
+  }
+  b->n_tiles = (int)t.size();
+  cudaFree(b->tiles);
+  cudaFree(b->tile_inst);
+  b->tiles = nullptr;
+  b->tile_inst = nullptr;
+  BCUDA(b, cudaMalloc((void **)&b->tiles, sizeof(TileDesc) * std::max<size_t>(1, t.size())));
+  BCUDA(b, cudaMalloc((void **)&b->tile_inst, sizeof(int) * std::max<size_t>(1, ti.size())));
+  if (!t.empty()) {
+    BCUDA(b, cudaMemcpy(b->tiles, t.data(), sizeof(TileDesc) * t.size(), cudaMemcpyHostToDevice));
+    BCUDA(b, cudaMemcpy(b->tile_inst, ti.data(), sizeof(int) * ti.size(), cudaMemcpyHostToDevice));
+  }
+  return LBM_OK;
+}
+
+static int batch_upload_args(lbm_batch *b) {
+  const int n = (int)b->ctx.size();
+  const bool f64 = b->precision == LBM_F64;
+  const size_t one = f64 ? sizeof(SweepArgs<double>) : sizeof(SweepArgs<float>);
+  std::vector<unsigned char> h(one * n);
+  b->big = false;
+  for (int k = 0; k < n; ++k) {
+    lbm_ctx *c = b->ctx[k];
+    std::memcpy(h.data() + one * k, f64 ? (const void *)&c->a64 : (const void *)&c->a32, one);
+    if ((long long)c->Q * slot_stride(c->N) >= (1LL << 31)) b->big = true;
+    b->versions[k] = c->version;
+  }
+  if (!b->inst) BCUDA(b, cudaMalloc(&b->inst, one * n));
+  BCUDA(b, cudaMemcpy(b->inst, h.data(), one * n, cudaMemcpyHostToDevice));
+  return LBM_OK;
+}
+
+static int batch_refresh_if_needed(lbm_batch *b) {
+  bool stale = false;
+  for (size_t k = 0; k < b->ctx.size(); ++k) stale |= b->ctx[k]->version != b->versions[k];
+  if (!stale) return LBM_OK;
+  // geometry may have changed: fetch the tile lists again
+  for (size_t k = 0; k < b->ctx.size(); ++k) {
+    lbm_ctx *c = b->ctx[k];
+    b->host_tiles[k].resize(c->n_tiles);
+    if (c->n_tiles)
+      BCUDA(b, cudaMemcpy(b->host_tiles[k].data(), c->tiles, sizeof(TileDesc) * c->n_tiles,
+                          cudaMemcpyDeviceToHost));
+  }
+  int rc = batch_upload(b);
+  if (rc == LBM_OK) rc = batch_upload_args(b);
+  batch_drop_graph(b);
+  return rc;
+}
+
+static cudaError_t batch_launch(lbm_batch *b, bool odd, bool prepare_only) {
+  return b->lattice == LBM_D2Q9
+             ? launch_sweep_batch_d2q9(b->precision, odd, b->inst, b->tiles, b->tile_inst, b->n_tiles,
+                                       b->big, b->blocks_per_sm, b->stream, prepare_only)
+             : launch_sweep_batch_d3q19(b->precision, odd, b->inst, b->tiles, b->tile_inst,
+                                        b->n_tiles, b->big, b->blocks_per_sm, b->stream, prepare_only);
+}
+
+static int batch_check_parity(lbm_batch *b, bool *odd) {
+  const long long t0 = b->ctx[0]->t;
+  for (lbm_ctx *c : b->ctx) {
+    if (!c->geometry_set) return bfail(b, LBM_ESTATE, "a context of the batch has no geometry");
+    if ((c->t & 1) != (t0 & 1))
+      return bfail(b, LBM_ESTATE, "contexts of a batch must be at the same time parity");
+  }
+  *odd = (t0 & 1) != 0;
+  return LBM_OK;
+}
+
+static int batch_run_plain(lbm_batch *b, int n) {
+  bool odd;
+  int rc = batch_check_parity(b, &odd);
+  if (rc != LBM_OK) return rc;
+  for (int k = 0; k < n; ++k) {
+    BCUDA(b, batch_launch(b, ((k & 1) != 0) != odd, false));
+  }
+  for (lbm_ctx *c : b->ctx) c->t += n;
+  return LBM_OK;
+}
+
+extern "C" {
+
+int lbm_batch_create(lbm_batch **out, int n, lbm_ctx *const *ctxs) {
+  if (!out) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: out is NULL");
+  *out = nullptr;
+  if (n < 1 || !ctxs) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: empty batch");
+  for (int k = 0; k < n; ++k) {
+    if (!ctxs[k]) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: context %d is NULL", k);
+    if (ctxs[k]->lattice != ctxs[0]->lattice || ctxs[k]->precision != ctxs[0]->precision ||
+        ctxs[k]->device != ctxs[0]->device)
+      return bfail(nullptr, LBM_EINVAL,
+                   "lbm_batch_create: contexts must share lattice, precision and device");
+    for (int j = 0; j < k; ++j)
+      if (ctxs[j] == ctxs[k]) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: context %d repeated", k);
+  }
+  lbm_batch *b = new (std::nothrow) lbm_batch();
+  if (!b) return bfail(nullptr, LBM_ENOMEM, "lbm_batch_create: host allocation");
+  b->ctx.assign(ctxs, ctxs + n);
+  b->lattice = ctxs[0]->lattice;
+  b->precision = ctxs[0]->precision;
+  b->device = ctxs[0]->device;
+  b->stream = ctxs[0]->stream;
+  b->host_tiles.resize(n);
+  b->versions.assign(n, -1);
+  cudaSetDevice(b->device);
+  const int rc = batch_refresh_if_needed(b);
+  if (rc != LBM_OK) {
+    g_create_error = b->err;
+    lbm_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return LBM_OK;
+}
+
+int lbm_batch_destroy(lbm_batch *b) {
+  if (!b) return LBM_OK;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_drop_graph(b);
+  cudaFree(b->inst);
+  cudaFree(b->tiles);
+  cudaFree(b->tile_inst);
+  delete b;
+  return LBM_OK;
+}
+
+int lbm_batch_set_stream(lbm_batch *b, void *stream) {
+  if (!b) return LBM_EINVAL;
+  b->stream = static_cast<cudaStream_t>(stream);
+  batch_drop_graph(b);
+  return LBM_OK;
+}
+
+int lbm_batch_set_config(lbm_batch *b, int order, int blocks_per_sm) {
+  if (!b) return LBM_EINVAL;
+  if (order < 0 || order > 2 || blocks_per_sm < 0 || blocks_per_sm > 32)
+    return bfail(b, LBM_EINVAL, "lbm_batch_set_config: order in 0..2, blocks_per_sm in 0..32");
+  cudaSetDevice(b->device);
+  b->order = order;
+  b->blocks_per_sm = blocks_per_sm;
+  batch_drop_graph(b);
+  return batch_upload(b);
+}
+
+int lbm_batch_step(lbm_batch *b, int n) {
+  if (!b) return LBM_EINVAL;
+  if (n < 0) return bfail(b, LBM_EINVAL, "lbm_batch_step: n < 0");
+  cudaSetDevice(b->device);
+  int rc = batch_refresh_if_needed(b);
+  if (rc != LBM_OK) return rc;
+  bool odd;
+  if ((rc = batch_check_parity(b, &odd)) != LBM_OK) return rc;
+  if (n < 2) return batch_run_plain(b, n);
+  // a graph of one even+odd pair of launches starting at the current parity
+  if (!b->graph || b->graph_odd != odd) {
+    batch_drop_graph(b);
+    BCUDA(b, batch_launch(b, odd, true));    // launch attributes before the capture
+    BCUDA(b, batch_launch(b, !odd, true));
+    cudaStream_t cap = b->stream;
+    bool own = false;
+    if (cap == nullptr) {  // the legacy stream cannot be captured: use a private one
+      BCUDA(b, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+      own = true;
+    }
+    cudaGraph_t g = nullptr;
+    BCUDA(b, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    cudaStream_t saved = b->stream;
+    b->stream = cap;
+    cudaError_t e1 = batch_launch(b, odd, false);
+    cudaError_t e2 = batch_launch(b, !odd, false);
+    b->stream = saved;
+    cudaError_t e3 = cudaStreamEndCapture(cap, &g);
+    if (own) cudaStreamDestroy(cap);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return bfail(b, LBM_ECUDA, "lbm_batch_step: graph capture failed: %s",
+                   cudaGetErrorString(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3)));
+    }
+    cudaError_t e4 = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e4 != cudaSuccess) {
+      b->graph = nullptr;
+      return bfail(b, LBM_ECUDA, "lbm_batch_step: %s", cudaGetErrorString(e4));
+    }
+    b->graph_odd = odd;
+    b->graph_pairs = 1;
+  }
+  for (int k = 0; k + 1 < n; k += 2) BCUDA(b, cudaGraphLaunch(b->graph, b->stream));
+  for (lbm_ctx *c : b->ctx) c->t += n - (n & 1);
+  if (n & 1) return batch_run_plain(b, 1);
+  return LBM_OK;
+}
+
+int lbm_batch_tune(lbm_batch *b, int trial_steps, int *order_out, int *blocks_out) {
+  if (!b) return LBM_EINVAL;
+  if (trial_steps < 2) return bfail(b, LBM_EINVAL, "lbm_batch_tune: trial_steps >= 2");
+  trial_steps &= ~1;
+  cudaSetDevice(b->device);
+  int rc = batch_refresh_if_needed(b);
+  if (rc != LBM_OK) return rc;
+  bool odd;
+  if ((rc = batch_check_parity(b, &odd)) != LBM_OK) return rc;
+  // snapshot populations and link buffers: tuning leaves the state untouched
+  size_t bytes = 0;
+  for (lbm_ctx *c : b->ctx)
+    bytes += pop_alloc_bytes(c) + (size_t)store_bytes(c->precision) * std::max<long long>(1, c->n_links);
+  void *snap = nullptr;
+  BCUDA(b, cudaMalloc(&snap, bytes));
+  auto copy_state = [&](bool save) -> cudaError_t {
+    size_t o = 0;
+    for (lbm_ctx *c : b->ctx) {
+      const size_t pb = pop_alloc_bytes(c);
+      const size_t lb = (size_t)store_bytes(c->precision) * std::max<long long>(1, c->n_links);
+      char *s = static_cast<char *>(snap) + o;
+      cudaError_t e = save ? cudaMemcpyAsync(s, c->pop_alloc, pb, cudaMemcpyDeviceToDevice, b->stream)
+                           : cudaMemcpyAsync(c->pop_alloc, s, pb, cudaMemcpyDeviceToDevice, b->stream);
+      if (e != cudaSuccess) return e;
+      if (c->lnk) {
+        e = save ? cudaMemcpyAsync(s + pb, c->lnk, lb, cudaMemcpyDeviceToDevice, b->stream)
+                 : cudaMemcpyAsync(c->lnk, s + pb, lb, cudaMemcpyDeviceToDevice, b->stream);
+        if (e != cudaSuccess) return e;
+      }
+      o += pb + lb;
+    }
+    return cudaSuccess;
+  };
+  cudaError_t e = copy_state(true);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int orders[3] = {0, 1, 2};
+  const int blocks[3] = {0, 4, 3};
+  float best = 1e30f;
+  int best_o = b->order, best_b = b->blocks_per_sm;
+  for (int oi = 0; oi < 3 && e == cudaSuccess; ++oi)
+    for (int bi = 0; bi < 3 && e == cudaSuccess; ++bi) {
+      b->order = orders[oi];
+      b->blocks_per_sm = blocks[bi];
+      if ((rc = batch_upload(b)) != LBM_OK) break;
+      for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = batch_launch(b, (k & 1) != odd, false);  // warm
+      if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+      for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) e = batch_launch(b, (k & 1) != odd, false);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms < best) {
+        best = ms;
+        best_o = orders[oi];
+        best_b = blocks[bi];
+      }
+      if (e == cudaSuccess) e = copy_state(false);
+    }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  cudaFree(snap);
+  if (rc != LBM_OK) return rc;
+  if (e != cudaSuccess) return bfail(b, LBM_ECUDA, "lbm_batch_tune: %s", cudaGetErrorString(e));
+  b->order = best_o;
+  b->blocks_per_sm = best_b;
+  batch_drop_graph(b);
+  if ((rc = batch_upload(b)) != LBM_OK) return rc;
+  if (order_out) *order_out = best_o;
+  if (blocks_out) *blocks_out = best_b;
+  return LBM_OK;
+}
+
+int lbm_batch_query(const lbm_batch *b, int *n_contexts, int64_t *tiles, int *order,
+                    int *blocks_per_sm) {
+  if (!b) return LBM_EINVAL;
+  if (n_contexts) *n_contexts = (int)b->ctx.size();
+  if (tiles) *tiles = b->n_tiles;
+  if (order) *order = b->order;
+  if (blocks_per_sm) *blocks_per_sm = b->blocks_per_sm;
+  return LBM_OK;
+}
+
+const char *lbm_batch_last_error(const lbm_batch *b) {
+  return b ? b->err.c_str() : g_create_error.c_str();
 }
 
 }  // extern "C"

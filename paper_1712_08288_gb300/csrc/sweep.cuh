@@ -390,10 +390,20 @@ __device__ __forceinline__ constexpr int aligned_window_offset(int ex) {
   return ex > 0 ? 16 / (int)sizeof(T) - 1 : (ex < 0 ? 1 : 0);
 }
 
-template <class L, class T, bool ODD, bool SKEW, bool ALIGNED, class I>
+// Arguments of the instance a tile belongs to: the kernel parameter for a single
+// context, an entry of the instance table for a batch.
+template <bool BATCH, class C>
+__device__ __forceinline__ const SweepArgs<C> &args_for(const SweepArgs<C> &a, const SweepArgs<C> *inst,
+                                                       const int *tile_inst, int tile) {
+  if constexpr (BATCH) return inst[tile_inst[tile]];
+  else return a;
+}
+
+template <class L, class T, bool ODD, bool SKEW, bool ALIGNED, class I, bool BATCH>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
     sweep_kernel(const SweepArgs<typename Storage<T>::C> a, const TileDesc *__restrict__ tiles,
-                 int n_tiles) {
+                 int n_tiles, const SweepArgs<typename Storage<T>::C> *__restrict__ inst,
+                 const int *__restrict__ tile_inst) {
   using C = typename Storage<T>::C;
   using SL = StageLayout<L, T>;
   constexpr int Q = L::Q;
@@ -416,31 +426,33 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
   for (int s = 0; s < NS; ++s) {
     const int tile = gw + s * nw;
     if (tile < n_tiles)
-      issue_tile<L, T, ODD, I>(a, tiles[tile], wsm + s * SL::kStage, offs + s * NO, &bars[s]);
+      issue_tile<L, T, ODD, I>(args_for<BATCH>(a, inst, tile_inst, tile), tiles[tile],
+                               wsm + s * SL::kStage, offs + s * NO, &bars[s]);
   }
 
-  T *__restrict__ pop = static_cast<T *>(a.pop);
-  const I S = (I)a.S;
-  const int nxm1 = a.nx - 1;
-  const LinkCoef<C> *coef = static_cast<const LinkCoef<C> *>(a.geo.coef);
-  T *const lnk = static_cast<T *>(a.geo.lnk);
   int k = 0;
   for (int tile = gw; tile < n_tiles; tile += nw, ++k) {
     const int s = k % NS;
     const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)(k / NS) & 1u);
     if (__any_sync(0xffffffffu, !ok)) {
       // a copy did not land in time: flag it, drain what this warp issued, stop
-      if (lane == 0) atomicOr(a.status, 2);
+      if (lane == 0) atomicOr(args_for<BATCH>(a, inst, tile_inst, tile).status, 2);
       for (int j = 0; j < NS; ++j)
         if (tile + j * nw < n_tiles) mbar_wait_bounded(&bars[(k + j) % NS], (uint32_t)((k + j) / NS) & 1u);
       return;
     }
+    const SweepArgs<C> &A = args_for<BATCH>(a, inst, tile_inst, tile);
+    T *__restrict__ pop = static_cast<T *>(A.pop);
+    const I S = (I)A.S;
+    const int nxm1 = A.nx - 1;
+    const LinkCoef<C> *coef = static_cast<const LinkCoef<C> *>(A.geo.coef);
+    T *const lnk = static_cast<T *>(A.geo.lnk);
     const TileDesc td = tiles[tile];
     const int y = td.yz & 0xffff, z = td.yz >> 16;
     const unsigned char *stg = wsm + s * SL::kStage;
     const T *st = reinterpret_cast<const T *>(stg);
     const uint32_t *rec_s = reinterpret_cast<const uint32_t *>(stg + SL::kRec) + offs[s * NO + Q];
-    const int row = a.nx * (y + a.ny * z);
+    const int row = A.nx * (y + A.ny * z);
 #pragma unroll 1
     for (int j = 0; j < kNodesPerLane; ++j) {
     const int xl = j * 32 + lane;          // position inside the tile
@@ -465,7 +477,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
       __syncwarp();   // stage s consumed: refill it with the tile NS rounds ahead
       const int nt = tile + NS * nw;
       if (nt < n_tiles)
-        issue_tile<L, T, ODD, I>(a, tiles[nt], wsm + s * SL::kStage, offs + s * NO, &bars[s]);
+        issue_tile<L, T, ODD, I>(args_for<BATCH>(a, inst, tile_inst, nt), tiles[nt],
+                                 wsm + s * SL::kStage, offs + s * NO, &bars[s]);
     }
     if (solid) continue;
 
@@ -476,8 +489,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
       for (int i = 0; i < Q; ++i) {
         const int ex = L::ex(i);
         if ((ex > 0 && xlo) || (ex < 0 && xhi)) {
-          const long long src = wrap_index(x, y, z, -ex, -L::ey(i), -L::ez(i), a.nx, a.ny, a.nz,
-                                           a.sy, a.sz);
+          const long long src = wrap_index(x, y, z, -ex, -L::ey(i), -L::ez(i), A.nx, A.ny, A.nz,
+                                           A.sy, A.sz);
           g[i] = Storage<T>::load(pop + (I)L::opp(i) * S + (I)src);
         }
       }
@@ -493,31 +506,31 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
 
     C gp[Q];
     C drho;
-    collide<L, C>(g, gp, a, drho);
-    if (!(fabs(drho) < C(1e6))) atomicOr(a.status, 1);
+    collide<L, C>(g, gp, A, drho);
+    if (!(fabs(drho) < C(1e6))) atomicOr(A.status, 1);
 
     T *const pn = pop + n;
     if (!ODD) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) Storage<T>::store(pn + (I)a.koff_even[i], gp[i]);   // slot opp(i) of x
+      for (int i = 0; i < Q; ++i) Storage<T>::store(pn + (I)A.koff_even[i], gp[i]);   // slot opp(i) of x
     } else {
       // rows y +- 1, z +- 1 stay inside the grid for the whole tile: constant offsets
       const bool rows_inside =
-          y > 0 && y < a.ny - 1 && (L::D == 2 || (z > 0 && z < a.nz - 1));
+          y > 0 && y < A.ny - 1 && (L::D == 2 || (z > 0 && z < A.nz - 1));
       if (rows_inside) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
           const int ex = L::ex(i);
           if ((ex > 0 && xhi) || (ex < 0 && xlo)) continue;   // crosses the x-wrap
-          Storage<T>::store(pn + (I)a.koff_odd[i], gp[i]);     // slot i of x + e_i
+          Storage<T>::store(pn + (I)A.koff_odd[i], gp[i]);     // slot i of x + e_i
         }
         if (xlo || xhi) {
 #pragma unroll
           for (int i = 0; i < Q; ++i) {
             const int ex = L::ex(i);
             if ((ex > 0 && xhi) || (ex < 0 && xlo)) {
-              const long long dn = wrap_index(x, y, z, ex, L::ey(i), L::ez(i), a.nx, a.ny, a.nz,
-                                              a.sy, a.sz);
+              const long long dn = wrap_index(x, y, z, ex, L::ey(i), L::ez(i), A.nx, A.ny, A.nz,
+                                              A.sy, A.sz);
               Storage<T>::store(pop + (I)i * S + (I)dn, gp[i]);
             }
           }
@@ -526,8 +539,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
         // rows of the tile touch a periodic edge in y or z: wrap every neighbour
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-          const long long dn = wrap_index(x, y, z, L::ex(i), L::ey(i), L::ez(i), a.nx, a.ny, a.nz,
-                                          a.sy, a.sz);
+          const long long dn = wrap_index(x, y, z, L::ex(i), L::ey(i), L::ez(i), A.nx, A.ny, A.nz,
+                                          A.sy, A.sz);
           Storage<T>::store(pop + (I)i * S + (I)dn, gp[i]);
         }
       }
@@ -541,7 +554,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
           const int kk = boff + __popc(bmask & ((1u << dd) - 1u));
           const LinkCoef<C> c = coef[kk];
           const int i = L::opp(dd);
-          const C v = a.one_minus_b * g[i] + c.a * g[dd] + c.bb * gp[i] + c.c * gp[dd] + c.w;
+          const C v = A.one_minus_b * g[i] + c.a * g[dd] + c.bb * gp[i] + c.c * gp[dd] + c.w;
           if (!ODD) Storage<T>::store(lnk + kk, v);          // read by the next odd step
           else Storage<T>::store(pn + (I)i * S, v);          // slot i of x_f itself
         }
@@ -569,12 +582,20 @@ int persistent_blocks(int threads, size_t smem) {
 }
 
 template <auto Kernel, class A>
-void launch_persistent(const A &a, const TileDesc *tiles, int n_tiles, size_t smem, cudaStream_t st) {
+void launch_persistent(const A &a, const TileDesc *tiles, int n_tiles, size_t smem, cudaStream_t st,
+                       const A *inst = nullptr, const int *tile_inst = nullptr, int blocks_per_sm = 0,
+                       bool prepare_only = false) {
   const int threads = kWarpsPerBlock * 32;
   int grid = persistent_blocks<Kernel>(threads, smem);
+  if (blocks_per_sm > 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (blocks_per_sm * sms < grid) grid = blocks_per_sm * sms;
+  }
   const int need = (n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (grid > need) grid = need;
-  Kernel<<<grid, threads, smem, st>>>(a, tiles, n_tiles);
+  if (!prepare_only) Kernel<<<grid, threads, smem, st>>>(a, tiles, n_tiles, inst, tile_inst);
 }
 
 template <class L, class T>
@@ -588,8 +609,8 @@ cudaError_t launch_sweep_t(bool odd, const SweepArgs<typename Storage<T>::C> &a,
   const bool aligned = ((long long)a.nx * (long long)sizeof(T)) % 16 == 0;
 #define LBM_LAUNCH(O, S, I)                                                              \
   do {                                                                                   \
-    if (aligned) launch_persistent<sweep_kernel<L, T, O, S, true, I>>(a, tiles, n_tiles, smem, st);   \
-    else launch_persistent<sweep_kernel<L, T, O, S, false, I>>(a, tiles, n_tiles, smem, st);         \
+    if (aligned) launch_persistent<sweep_kernel<L, T, O, S, true, I, false>>(a, tiles, n_tiles, smem, st);   \
+    else launch_persistent<sweep_kernel<L, T, O, S, false, I, false>>(a, tiles, n_tiles, smem, st);         \
   } while (0)
   if (big) {
     if (odd) { if (skew) LBM_LAUNCH(true, true, long long); else LBM_LAUNCH(true, false, long long); }
@@ -599,6 +620,29 @@ cudaError_t launch_sweep_t(bool odd, const SweepArgs<typename Storage<T>::C> &a,
     else LBM_LAUNCH(false, false, int);
   }
 #undef LBM_LAUNCH
+  return cudaGetLastError();
+}
+
+// One step of a batch: the tiles of all instances in one persistent launch, each
+// tile reading its instance's arguments from the table.  Instances may differ in
+// size, alignment and skew; the unaligned-window path serves all of them.
+// prepare_only: set up the kernels' launch attributes without launching (done once
+// before a stream capture).
+template <class L, class T>
+cudaError_t launch_sweep_batch_t(bool odd, const SweepArgs<typename Storage<T>::C> *inst,
+                                 const TileDesc *tiles, const int *tile_inst, int n_tiles,
+                                 bool big, int blocks_per_sm, cudaStream_t st, bool prepare_only) {
+  if (n_tiles == 0) return cudaSuccess;
+  using A = SweepArgs<typename Storage<T>::C>;
+  const size_t smem = kWarpsPerBlock * warp_smem_bytes<L, T>();
+  A dummy{};
+#define LBM_LAUNCH_B(O, I)                                                                       \
+  launch_persistent<sweep_kernel<L, T, O, true, false, I, true>>(dummy, tiles, n_tiles, smem, st, \
+                                                                 inst, tile_inst, blocks_per_sm, \
+                                                                 prepare_only)
+  if (big) { if (odd) LBM_LAUNCH_B(true, long long); else LBM_LAUNCH_B(false, long long); }
+  else { if (odd) LBM_LAUNCH_B(true, int); else LBM_LAUNCH_B(false, int); }
+#undef LBM_LAUNCH_B
   return cudaGetLastError();
 }
 

@@ -342,6 +342,17 @@ def couette_ensemble(count=96, seed=0):
     return out
 
 
+def ensemble_member(p, lattice="D2Q9"):
+    """Inputs of one ensemble instance (a dict of couette_ensemble)."""
+    w = couette_2d(p["n"], p["center"], p["R1"], p["R2"], p["U1"], lattice)
+    w["nu"] = p["nu"]
+    w["s_nu"] = s_nu_for(p["nu"])
+    w["S"] = relaxation_rates(lattice, w["s_nu"])
+    w["rho0"] = 1.0
+    w["force"] = (0.0, 0.0, 0.0)
+    return w
+
+
 def fluid_count(solid):
     return int((~np.asarray(solid, dtype=bool)).sum())
 
