@@ -10,6 +10,8 @@ Layout
 ------
 ``lattices``  velocity sets, weights, MRT matrices (Appendix; D3Q19 from the
               d'Humieres et al. 2002 polynomial basis the Appendix cites).
+``adjoint``   reverse-mode (discrete adjoint) of ``lbm`` for a velocity-mismatch
+              loss; gradients with respect to S, per-link q and wall velocity.
 ``lbm``       one lattice-Boltzmann step: MRT collision (Appendix), equilibrium
               Eq. (42), advection Eq. (2.2b), the boundary scheme Eq. (2.13) built
               from Eqs. (2.5)-(2.7) and (2.9) in the paper's order, moments and the
@@ -27,4 +29,4 @@ plots are not available, so the oracle's absolute error values are not pinned to
 paper (only their order of convergence is).
 """
 
-from . import lattices, lbm  # noqa: F401
+from . import adjoint, lattices, lbm  # noqa: F401

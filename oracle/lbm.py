@@ -143,7 +143,7 @@ def boundary_value(w_i, e_i, gamma, l, b, rho0, phi,
     # t+dt is the advected f'_ibar(x_f, t)
     f_ibar_x2 = (1 + l - 2 * gamma) * f_ibar_next + (2 * gamma - l) * fpost_ibar
     # Eq. (2.6): half-way bounce-back across x_b, which lies midway between x_1, x_2
-    e_dot_phi = (np.asarray(e_i, dtype=np.float64) * np.asarray(phi, dtype=np.float64)).sum(axis=-1)
+    e_dot_phi = (np.asarray(e_i) * np.asarray(phi)).sum(axis=-1)
     f_i_x1 = f_ibar_x2 + 2 * w_i * rho0 * e_dot_phi / CS2
     # Eq. (2.5): interpolation at x_f between x_l (advected f'_i(x_f,t)) and x_1
     rhs = l / (1 + l) * fpost_i + 1 / (1 + l) * f_i_x1
@@ -177,6 +177,7 @@ class Simulation:
         self.skew = tuple(int(s) for s in skew)
         self.nbr = neighbour_table(lat, self.shape, self.skew)
         c0, c1, c2, b = scheme
+        self.scheme_coeffs = (float(c0), float(c1), float(c2))
         self.b = float(b)
         assert 0.0 < self.b <= 1.0, "b must lie in (0, 1] (Eq. (2.13))"
 
