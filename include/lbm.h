@@ -186,7 +186,37 @@ int lbm_error_norms(lbm_ctx *ctx, const double *u_ref, lbm_norms *out);
  * that overlap on the GPU race on it, so issue them in order on one stream. */
 int lbm_error_norms_noalloc(lbm_ctx *ctx, const double *u_ref_dev, double *out_dev);
 
-/* Batches (ensembles of independent problems).  A batch advances several contexts
+/* Replace the relaxation rates (no reset of the populations). */
+int lbm_set_relaxation(lbm_ctx *ctx, const double *s);
+
+/* Replace the wall fractions and/or wall velocities of the existing cut links
+ * (same list, same order as given to lbm_set_geometry; NULL keeps the current
+ * values), with the checks of lbm_set_geometry and lbm_set_scheme.  The
+ * populations are not reset. */
+int lbm_set_link_values(lbm_ctx *ctx, const double *q, const double *uw);
+
+/* Discrete adjoint of n_steps time steps from the current state (reverse mode of
+ * exactly what lbm_step computes), for the loss
+ *   J = sum over fluid nodes n with mask[n] != 0 of |u(x_n, T) - u_target(x_n)|^2,
+ * u the reported velocity after the n_steps (T = current time + n_steps).
+ * The forward run keeps a raw checkpoint every checkpoint_every steps (0 = about
+ * sqrt(n_steps)); the backward pass recomputes one segment at a time from its
+ * checkpoint and runs the adjoint sweep through it.  On return the context is in
+ * the state after the forward run (as if lbm_step(n_steps) had been called).
+ *   mask      nodes bytes (host); u_target D*nodes doubles (host, node-major).
+ *   loss      J (may be NULL).
+ *   grad_s    Q doubles: dJ/ds_k (0 for the conserved rows), or NULL.
+ *   grad_q    n_links doubles: dJ/dq per link in the order given to
+ *             lbm_set_geometry, or NULL.
+ *   grad_uw   3*n_links doubles: dJ/dphi per link, or NULL.
+ * The adjoint computes in double for LBM_F64 and in float otherwise; gradients
+ * are accumulated in double.  Memory: about (n_steps/checkpoint_every +
+ * checkpoint_every + 3) population arrays. */
+int lbm_adjoint(lbm_ctx *ctx, int n_steps, int checkpoint_every, const uint8_t *mask,
+                const double *u_target, double *loss, double *grad_s, double *grad_q,
+                double *grad_uw);
+
+/* Batches (ensembles of independent problems)./* Batches (ensembles of independent problems).  A batch advances several contexts
  * -- same lattice, precision and device, any sizes, geometries and parameters --
  * by ONE persistent sweep launch per time step that walks the tiles of all of them,
  * replayed from a CUDA graph holding an even and an odd step.  Each context keeps

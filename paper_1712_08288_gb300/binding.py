@@ -26,6 +26,7 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_set_skew", "lbm_s
            "lbm_set_scheme", "lbm_set_force", "lbm_init_equilibrium", "lbm_set_populations",
            "lbm_get_populations", "lbm_step", "lbm_time", "lbm_moments", "lbm_moments_device",
            "lbm_error_norms", "lbm_error_norms_noalloc", "lbm_query", "lbm_last_error",
+           "lbm_set_relaxation", "lbm_set_link_values", "lbm_adjoint",
            "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_set_stream", "lbm_batch_set_config",
            "lbm_batch_tune", "lbm_batch_step", "lbm_batch_query", "lbm_batch_last_error"]
 
@@ -59,6 +60,9 @@ def load_library(path=LIB_PATH):
         "lbm_error_norms_noalloc": (I, [P, P, P]),
         "lbm_query": (I, [P, P, P, P, P, P]),
         "lbm_last_error": (ct.c_char_p, [P]),
+        "lbm_set_relaxation": (I, [P, P]),
+        "lbm_set_link_values": (I, [P, P, P]),
+        "lbm_adjoint": (I, [P, I, I, P, P, P, P, P, P]),
         "lbm_batch_create": (I, [ct.POINTER(P), I, P]),
         "lbm_batch_destroy": (I, [P]),
         "lbm_batch_set_stream": (I, [P, P]),
@@ -203,12 +207,64 @@ class Lbm:
         self._check(self._lib.lbm_error_norms_noalloc(self.h, ct.c_void_p(u_ref_dev_ptr),
                                                       ct.c_void_p(out_dev_ptr)))
 
+    def set_relaxation(self, s):
+        s = np.ascontiguousarray(s, dtype=np.float64)
+        assert s.shape == (self.Q,)
+        self._check(self._lib.lbm_set_relaxation(self.h, _ptr(s)))
+
+    def set_link_values(self, q=None, uw=None):
+        q = None if q is None else np.ascontiguousarray(q, dtype=np.float64)
+        uw = None if uw is None else np.ascontiguousarray(np.asarray(uw, dtype=np.float64).reshape(-1, 3))
+        self._check(self._lib.lbm_set_link_values(self.h, _ptr(q), _ptr(uw)))
+
+    def adjoint(self, n_steps, mask, u_target, checkpoint_every=0):
+        """lbm_adjoint: (J, dJ/ds (Q,), dJ/dq (links,), dJ/dphi (links, 3))."""
+        nl = self.query()["links"]
+        mask = np.ascontiguousarray(np.asarray(mask).reshape(self.N), dtype=np.uint8)
+        ut = np.ascontiguousarray(np.asarray(u_target, dtype=np.float64).reshape(self.N, -1)[:, : self.D])
+        J = ct.c_double()
+        gs = np.zeros(self.Q)
+        gq = np.zeros(nl)
+        gp = np.zeros((nl, 3))
+        self._check(self._lib.lbm_adjoint(self.h, int(n_steps), int(checkpoint_every), _ptr(mask), _ptr(ut),
+                                          ct.byref(J), _ptr(gs), _ptr(gq), _ptr(gp)))
+        return J.value, gs, gq, gp
+
     def query(self):
         Q, D = ct.c_int(), ct.c_int()
         n, nf, nl = ct.c_int64(), ct.c_int64(), ct.c_int64()
         self._check(self._lib.lbm_query(self.h, ct.byref(Q), ct.byref(D), ct.byref(n), ct.byref(nf),
                                         ct.byref(nl)))
         return dict(Q=Q.value, D=D.value, nodes=n.value, fluid_nodes=nf.value, links=nl.value)
+
+
+def adjoint_loss_function():
+    """A torch.autograd.Function whose forward runs n_steps from a fixed initial state
+    and returns J = sum_mask |u(T) - u_target|^2, and whose backward returns the
+    gradients the library's adjoint computed (dJ/dq per link, dJ/ds, dJ/dphi).
+
+    apply(q, s, uw, sim, f0, n_steps, mask, u_target, checkpoint_every) with q
+    (links,), s (Q,), uw (links, 3) float64 tensors; f0 the initial full populations
+    (Q, nodes) numpy array the run starts from.
+    """
+    import torch
+
+    class AdjointLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, q, s, uw, sim, f0, n_steps, mask, u_target, checkpoint_every=0):
+            sim.set_relaxation(s.detach().cpu().numpy())
+            sim.set_link_values(q.detach().cpu().numpy(), uw.detach().cpu().numpy())
+            sim.set_populations(f0)
+            J, gs, gq, gp = sim.adjoint(n_steps, mask, u_target, checkpoint_every)
+            ctx.save_for_backward(torch.from_numpy(gq), torch.from_numpy(gs), torch.from_numpy(gp))
+            return torch.tensor(J, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            gq, gs, gp = ctx.saved_tensors
+            return gJ * gq, gJ * gs, gJ * gp, None, None, None, None, None, None
+
+    return AdjointLoss
 
 
 class Batch:

@@ -77,6 +77,9 @@ struct lbm_ctx {
   std::vector<int32_t> link_dir;
   std::vector<double> link_q;
   std::vector<double> link_uw;  // 3 per link
+  std::vector<int64_t> link_src; // input position of the link at each device position
+  double *dev_link_q = nullptr;    // wall fraction per link (adjoint)
+  double *dev_link_ephi = nullptr; // e_i . phi per link (adjoint)
   long long n_links = 0, n_fluid = 0, n_boundary = 0;
 
   SweepArgs<double> a64;
@@ -224,6 +227,22 @@ static int upload_coefficients(lbm_ctx *c) {
     }
     return 0;
   });
+  {
+    std::vector<double> ephi(nl);
+    with_lat(c->lattice, [&](auto lat) {
+      using L = decltype(lat);
+      for (long long k = 0; k < nl; ++k) {
+        const int i = L::opp(c->link_dir[k]);
+        ephi[k] = L::ex(i) * c->link_uw[3 * k] + L::ey(i) * c->link_uw[3 * k + 1] +
+                  L::ez(i) * c->link_uw[3 * k + 2];
+      }
+      return 0;
+    });
+    if (!c->dev_link_q) CUDA_OR_FAIL(c, cudaMalloc((void **)&c->dev_link_q, sizeof(double) * nl));
+    if (!c->dev_link_ephi) CUDA_OR_FAIL(c, cudaMalloc((void **)&c->dev_link_ephi, sizeof(double) * nl));
+    CUDA_OR_FAIL(c, cudaMemcpy(c->dev_link_q, c->link_q.data(), sizeof(double) * nl, cudaMemcpyHostToDevice));
+    CUDA_OR_FAIL(c, cudaMemcpy(c->dev_link_ephi, ephi.data(), sizeof(double) * nl, cudaMemcpyHostToDevice));
+  }
   if (c->precision == LBM_F64) {
     CUDA_OR_FAIL(c, cudaMemcpy(c->coef, co.data(), sizeof(double) * co.size(),
                                cudaMemcpyHostToDevice));
@@ -241,6 +260,8 @@ static void free_geometry(lbm_ctx *c) {
   cudaFree(c->boff); c->boff = nullptr;
   cudaFree(c->coef); c->coef = nullptr;
   cudaFree(c->lnk); c->lnk = nullptr;
+  cudaFree(c->dev_link_q); c->dev_link_q = nullptr;
+  cudaFree(c->dev_link_ephi); c->dev_link_ephi = nullptr;
 }
 
 // Tile descriptors (see TileDesc) of every run of kTileW nodes along x that holds
@@ -488,11 +509,13 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *solid, int64_t n_links, const in
   c->link_dir.assign(n_links, 0);
   c->link_q.assign(n_links, 0.0);
   c->link_uw.assign(3 * n_links, 0.0);
+  c->link_src.assign(n_links, 0);
   for (long long k = 0; k < n_links; ++k) {
     const long long n = node[k];
     const int d = dir[k];
     const long long pos = boff[bidx[n]] + __builtin_popcount(mask[n] & ((1u << d) - 1u));
     c->link_dir[pos] = d;
+    c->link_src[pos] = k;
     c->link_q[pos] = q[k];
     if (uw)
       for (int a = 0; a < 3; ++a) c->link_uw[3 * pos + a] = uw[3 * k + a];
@@ -710,6 +733,171 @@ int lbm_error_norms_noalloc(lbm_ctx *c, const double *u_ref_dev, double *out_dev
                                      (c->t & 1) != 0, u_ref_dev, out_dev, c->stream, &why);
   if (rc != LBM_OK) return fail(c, rc, "lbm_error_norms_noalloc: %s", why);
   return LBM_OK;
+}
+
+int lbm_set_relaxation(lbm_ctx *c, const double *s) {
+  if (!c || !s) return LBM_EINVAL;
+  for (int k = 0; k < c->Q; ++k)
+    if (!std::isfinite(s[k]) || s[k] < 0 || s[k] > 2)
+      return fail(c, LBM_EINVAL, "lbm_set_relaxation: s[%d] = %g outside [0, 2]", k, s[k]);
+  for (int k = 0; k < c->Q; ++k) c->s[k] = s[k];
+  refresh_args(c);
+  return LBM_OK;
+}
+
+int lbm_set_link_values(lbm_ctx *c, const double *q, const double *uw) {
+  if (!c) return LBM_EINVAL;
+  if (!c->geometry_set) return fail(c, LBM_ESTATE, "lbm_set_link_values: geometry not set");
+  const long long nl = c->n_links;
+  std::vector<double> nq(c->link_q), nuw(c->link_uw);
+  for (long long pos = 0; pos < nl; ++pos) {
+    const long long k = c->link_src[pos];
+    if (q) {
+      if (!(q[k] > 0.0 && q[k] <= 1.0))
+        return fail(c, LBM_EINVAL, "lbm_set_link_values: link %lld: q = %g not in (0, 1]", k, q[k]);
+      const double l = l_of(c, q[k]);
+      if (l < 0) return fail(c, LBM_EINVAL, "lbm_set_link_values: link %lld: l < 0", k);
+      if (!c->allow_nonconvex && !convex(q[k], l))
+        return fail(c, LBM_ENONCONVEX, "lbm_set_link_values: link %lld: l = %g violates Eq. 2.12", k, l);
+      nq[pos] = q[k];
+    }
+    if (uw)
+      for (int a = 0; a < 3; ++a) {
+        if (!std::isfinite(uw[3 * k + a]))
+          return fail(c, LBM_EINVAL, "lbm_set_link_values: link %lld: non-finite wall velocity", k);
+        nuw[3 * pos + a] = uw[3 * k + a];
+      }
+  }
+  c->link_q.swap(nq);
+  c->link_uw.swap(nuw);
+  cudaSetDevice(c->device);
+  const int rc = upload_coefficients(c);
+  refresh_args(c);
+  return rc;
+}
+
+int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *mask,
+                const double *u_target, double *loss, double *grad_s, double *grad_q,
+                double *grad_uw) {
+  if (!c) return LBM_EINVAL;
+  if (n_steps < 1) return fail(c, LBM_EINVAL, "lbm_adjoint: n_steps >= 1");
+  if (!mask || !u_target) return fail(c, LBM_EINVAL, "lbm_adjoint: mask and u_target are required");
+  if (checkpoint_every < 0) return fail(c, LBM_EINVAL, "lbm_adjoint: checkpoint_every < 0");
+  if (!c->geometry_set) return fail(c, LBM_ESTATE, "lbm_adjoint: geometry not set");
+  cudaSetDevice(c->device);
+  const long long T = n_steps;
+  long long K = checkpoint_every;
+  if (K == 0) K = (long long)std::ceil(std::sqrt((double)T));
+  if (K > T) K = T;
+  const long long nseg = (T + K - 1) / K;
+  const size_t csize = c->precision == LBM_F64 ? sizeof(double) : sizeof(float);
+  const size_t state = (size_t)c->Q * c->N * csize;               // natural layout, compute type
+  const size_t raw_pop = pop_alloc_bytes(c);
+  const size_t raw_lnk = (size_t)store_bytes(c->precision) * std::max<long long>(1, c->n_links);
+  const long long nl = c->n_links;
+  char *ck = nullptr, *seg = nullptr, *fin = nullptr, *lam0 = nullptr, *lam1 = nullptr;
+  uint8_t *dmask = nullptr;
+  double *dut = nullptr, *dgs = nullptr, *dgq = nullptr, *dgp = nullptr, *dJ = nullptr;
+  std::vector<long long> tck(nseg);
+  int rc = LBM_OK;
+  auto cleanup = [&]() {
+    cudaFree(ck); cudaFree(seg); cudaFree(fin); cudaFree(lam0); cudaFree(lam1); cudaFree(dmask);
+    cudaFree(dut); cudaFree(dgs); cudaFree(dgq); cudaFree(dgp); cudaFree(dJ);
+  };
+#define ADJ_CUDA(call)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      cleanup();                                                                            \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s", #call, \
+                  cudaGetErrorString(e_));                                                  \
+    }                                                                                       \
+  } while (0)
+  ADJ_CUDA(cudaMalloc((void **)&ck, (raw_pop + raw_lnk) * nseg));
+  ADJ_CUDA(cudaMalloc((void **)&seg, state * K));
+  ADJ_CUDA(cudaMalloc((void **)&fin, raw_pop + raw_lnk));
+  ADJ_CUDA(cudaMalloc((void **)&lam0, state));
+  ADJ_CUDA(cudaMalloc((void **)&lam1, state));
+  ADJ_CUDA(cudaMalloc((void **)&dmask, c->N));
+  ADJ_CUDA(cudaMalloc((void **)&dut, sizeof(double) * c->N * c->D));
+  ADJ_CUDA(cudaMalloc((void **)&dgs, sizeof(double) * 19));
+  ADJ_CUDA(cudaMalloc((void **)&dgq, sizeof(double) * std::max<long long>(1, nl)));
+  ADJ_CUDA(cudaMalloc((void **)&dgp, sizeof(double) * 3 * std::max<long long>(1, nl)));
+  ADJ_CUDA(cudaMalloc((void **)&dJ, sizeof(double)));
+  cudaStream_t st = c->stream;
+  ADJ_CUDA(cudaMemcpyAsync(dmask, mask, c->N, cudaMemcpyHostToDevice, st));
+  ADJ_CUDA(cudaMemcpyAsync(dut, u_target, sizeof(double) * c->N * c->D, cudaMemcpyHostToDevice, st));
+  ADJ_CUDA(cudaMemsetAsync(dgs, 0, sizeof(double) * 19, st));
+  ADJ_CUDA(cudaMemsetAsync(dgq, 0, sizeof(double) * std::max<long long>(1, nl), st));
+  ADJ_CUDA(cudaMemsetAsync(dgp, 0, sizeof(double) * 3 * std::max<long long>(1, nl), st));
+  ADJ_CUDA(cudaMemsetAsync(dJ, 0, sizeof(double), st));
+  auto save_raw = [&](char *dst) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(dst, c->pop_alloc, raw_pop, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && c->lnk) e = cudaMemcpyAsync(dst + raw_pop, c->lnk, raw_lnk, cudaMemcpyDeviceToDevice, st);
+    return e;
+  };
+  auto load_raw = [&](const char *src) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(c->pop_alloc, src, raw_pop, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && c->lnk) e = cudaMemcpyAsync(c->lnk, src + raw_pop, raw_lnk, cudaMemcpyDeviceToDevice, st);
+    return e;
+  };
+  const long long t0 = c->t;
+  // forward pass with checkpoints every K steps
+  for (long long sgm = 0; sgm < nseg; ++sgm) {
+    ADJ_CUDA(save_raw(ck + (raw_pop + raw_lnk) * sgm));
+    tck[sgm] = c->t;
+    const int len = (int)std::min(K, T - sgm * K);
+    if ((rc = lbm_step(c, len)) != LBM_OK) { cleanup(); return rc; }
+  }
+  ADJ_CUDA(save_raw(fin));
+  // loss and lambda(T)
+  ADJ_CUDA(launch_export_state(c->lattice, c->precision, aux_args(c), (c->t & 1) != 0, seg, st));
+  ADJ_CUDA(launch_loss(c->lattice, c->precision, aux_args(c), seg, dmask, dut, lam0, dJ, st));
+  // backward pass: recompute each segment from its checkpoint, then step back
+  char *lin = lam0, *lout = lam1;
+  for (long long sgm = nseg - 1; sgm >= 0; --sgm) {
+    ADJ_CUDA(load_raw(ck + (raw_pop + raw_lnk) * sgm));
+    c->t = tck[sgm];
+    const int len = (int)std::min(K, T - sgm * K);
+    for (int r = 0; r < len; ++r) {
+      ADJ_CUDA(launch_export_state(c->lattice, c->precision, aux_args(c), (c->t & 1) != 0,
+                                   seg + state * r, st));
+      if ((rc = lbm_step(c, 1)) != LBM_OK) { cleanup(); return rc; }
+    }
+    for (int r = len - 1; r >= 0; --r) {
+      ADJ_CUDA(launch_adjoint_step(c->lattice, c->precision, c->a64, c->a32, aux_args(c),
+                                   c->dev_link_q, c->dev_link_ephi, dgq, dgp, dgs, c->c0, c->c1,
+                                   c->c2, c->b, c->rho0, c->s, seg + state * r, lin, lout, st));
+      std::swap(lin, lout);
+    }
+  }
+  // back to the state after the forward run
+  ADJ_CUDA(load_raw(fin));
+  c->t = t0 + T;
+  double hJ = 0.0;
+  std::vector<double> hgs(19), hgq(nl), hgp(3 * nl);
+  ADJ_CUDA(cudaMemcpyAsync(&hJ, dJ, sizeof(double), cudaMemcpyDeviceToHost, st));
+  ADJ_CUDA(cudaMemcpyAsync(hgs.data(), dgs, sizeof(double) * 19, cudaMemcpyDeviceToHost, st));
+  if (nl) {
+    ADJ_CUDA(cudaMemcpyAsync(hgq.data(), dgq, sizeof(double) * nl, cudaMemcpyDeviceToHost, st));
+    ADJ_CUDA(cudaMemcpyAsync(hgp.data(), dgp, sizeof(double) * 3 * nl, cudaMemcpyDeviceToHost, st));
+  }
+  ADJ_CUDA(cudaStreamSynchronize(st));
+  cleanup();
+#undef ADJ_CUDA
+  if (loss) *loss = hJ;
+  if (grad_s)
+    for (int k = 0; k < c->Q; ++k) grad_s[k] = with_lat(c->lattice, [&](auto lat) {
+      using L = decltype(lat);
+      return L::conserved(k) ? 0.0 : hgs[k];
+    });
+  for (long long pos = 0; pos < nl; ++pos) {
+    const long long k = c->link_src[pos];
+    if (grad_q) grad_q[k] = hgq[pos];
+    if (grad_uw)
+      for (int a = 0; a < 3; ++a) grad_uw[3 * k + a] = (a < c->D) ? hgp[3 * pos + a] : 0.0;
+  }
+  return check_status(c);
 }
 
 int lbm_query(const lbm_ctx *c, int *Q, int *D, int64_t *nodes, int64_t *fluid_nodes,

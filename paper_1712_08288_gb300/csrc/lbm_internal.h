@@ -128,6 +128,21 @@ cudaError_t launch_norm_partials(int lattice, int precision, const AuxArgs &a, b
                                  int n_blocks, cudaStream_t st);
 cudaError_t launch_norm_finish(const double *partials, int n_blocks, double *out,
                                cudaStream_t st);
+
+// adjoint (adjoint.cu); compute type double for precision 0, float otherwise
+cudaError_t launch_export_state(int lattice, int precision, const AuxArgs &a, bool odd, void *out,
+                                cudaStream_t st);
+cudaError_t launch_import_state(int lattice, int precision, const AuxArgs &a, const void *in,
+                                cudaStream_t st);
+cudaError_t launch_loss(int lattice, int precision, const AuxArgs &a, const void *g,
+                        const uint8_t *mask, const double *u_target, void *lam, double *J,
+                        cudaStream_t st);
+cudaError_t launch_adjoint_step(int lattice, int precision, const SweepArgs<double> &a64,
+                                const SweepArgs<float> &a32, const AuxArgs &a, const double *link_q,
+                                const double *link_ephi, double *grad_q, double *grad_phi,
+                                double *grad_s, double c0, double c1, double c2, double b,
+                                double rho0, const double *s, const void *f, const void *lam_in,
+                                void *lam_out, cudaStream_t st);
 int norm_blocks_for(long long N);
 
 }  // namespace lbm
