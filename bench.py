@@ -272,6 +272,11 @@ def run_gpu(args):
     if args.ensemble_steps > 0 and rank == 0:
         ens = run_ensemble(args, torch, stream)
 
+    # ---- adjoint: gradients through the whole run, sqrt(N) checkpointing --------
+    adj = None
+    if args.adjoint_steps > 0 and rank == 0:
+        adj = run_adjoint(args, torch, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_L, args.cpu_steps)
@@ -298,6 +303,7 @@ def run_gpu(args):
                      "note": "FP64 storage and arithmetic, same workload"},
             "accuracy": acc,
             "ensemble": ens,
+            "adjoint": adj,
             "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": clk.summary(),
@@ -369,6 +375,74 @@ def run_ensemble(args, torch, stream):
             "workload": "D2Q9 circular Couette ensemble, seed 0, n ~ U{48..768}, FP32 deviations"}
 
 
+def run_adjoint(args, torch, stream):
+    """Adjoint of the sphere-in-a-periodic-box problem (D3Q19, 128^3, sphere R=20 at
+    (64.37, 63.71, 64.13), body force 1e-6 along x, s_nu = 1): loss = sum over the slab
+    96 <= x < 104 of |u - u_target|^2 after K steps from rest, u_target from a run with
+    every wall fraction raised by 0.05 (clamped to 1) and s_nu scaled by 1.02.
+    FP32 timing: lbm_adjoint (forward with checkpoints + recompute + adjoint sweep)
+    against lbm_step over the same K steps.  FP64 check: dJ/ds_nu (sum over the
+    viscous rows) against central differences with h = 1e-4."""
+    from paper_1712_08288_gb300 import workloads as W
+    n, K = args.adjoint_L, args.adjoint_steps
+    c = (64.37 * n / 128, 63.71 * n / 128, 64.13 * n / 128)
+    w = W.sphere_3d(n, 20.0 * n / 128, c, s_nu=1.0, force=(1e-6, 0.0, 0.0))
+    N = n ** 3
+    x = np.arange(N) % n
+    mask = (x >= 96 * n // 128) & (x < 104 * n // 128)
+    viscous = [9, 11, 13, 14, 15]
+    wt = dict(w)
+    wt["links"] = dict(w["links"], q=np.minimum(w["links"]["q"] + 0.05, 1.0))
+    wt["S"] = w["S"].copy()
+    wt["S"][viscous] *= 1.02
+    tgt = build_sim(wt, "f64", torch, stream)
+    tgt.init_equilibrium()
+    tgt.step(K)
+    _, ut = tgt.moments()
+    ut = np.nan_to_num(ut)
+    del tgt
+    out = {"workload": "D3Q19 sphere R=%g in a periodic %d^3 box, %d steps" % (20.0 * n / 128, n, K)}
+    for prec in ("f32", "f64"):
+        sim = build_sim(w, prec, torch, stream)
+        sim.init_equilibrium()
+        sim.step(2)
+        sim.init_equilibrium()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.step(K)
+        torch.cuda.synchronize()
+        t_fwd = time.perf_counter() - t0
+        sim.init_equilibrium()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J, gs, gq, gp = sim.adjoint(K, mask, ut)
+        torch.cuda.synchronize()
+        t_adj = time.perf_counter() - t0
+        out[prec] = {"J": J, "dJ_ds_nu": float(gs[viscous].sum()),
+                     "forward_s": round(t_fwd, 4), "adjoint_total_s": round(t_adj, 4),
+                     "backward_over_forward": round((t_adj - t_fwd) / t_fwd, 2),
+                     "checkpoints": int(np.ceil(K / np.ceil(np.sqrt(K))))}
+        if prec == "f64":
+            h = 1e-4
+
+            def J_of(sv):
+                s2 = build_sim(w, "f64", torch, stream)
+                S = w["S"].copy()
+                S[viscous] = sv
+                s2.set_relaxation(S)
+                s2.init_equilibrium()
+                s2.step(K)
+                _, u = s2.moments()
+                d = u[mask] - ut[mask]
+                return float(np.nansum(d * d))
+            fd = (J_of(1.0 + h) - J_of(1.0 - h)) / (2 * h)
+            out["f64"]["fd_dJ_ds_nu"] = fd
+            out["f64"]["rel_err_vs_fd"] = abs(fd - out["f64"]["dJ_ds_nu"]) / abs(fd)
+        del sim
+    out["f32"]["rel_err_vs_f64"] = abs(out["f32"]["dJ_ds_nu"] - out["f64"]["dJ_ds_nu"]) / abs(out["f64"]["dJ_ds_nu"])
+    return out
+
+
 def _oracle_rate(L, steps, warmup):
     """Run the oracle in a fresh single-threaded process; returns (MLUPS, seconds)."""
     code = r"""
@@ -437,6 +511,8 @@ def main():
     ap.add_argument("--L", type=int, default=256)
     ap.add_argument("--accuracy-L", type=int, default=128)
     ap.add_argument("--accuracy-steps", type=int, default=20000)
+    ap.add_argument("--adjoint-L", type=int, default=128)
+    ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--ensemble-count", type=int, default=96)
     ap.add_argument("--ensemble-steps", type=int, default=400)
     ap.add_argument("--cpu-L", type=int, default=48)

@@ -19,59 +19,14 @@
 //     expression give the link gradients;
 //   collision (Appendix, MRT): with mu = M^-T lambda' (M^-T = diag(1/|M_k|^2) M),
 //     nu_k = (1 - s_k) mu_k for non-conserved rows and
-//     nu_k = mu_k + sum_l s_l (d meq_l / d m_k) mu_l for rho and j, where the
-//     derivatives of the equilibrium moments are obtained by evaluating the same
-//     meq() in forward-mode dual numbers; lambda(t) = M^T nu + boundary terms, and
+//     nu_k = mu_k + sum_l s_l (d meq_l / d m_k) mu_l for rho and j, with the
+//     derivatives of the closed-form equilibrium moments written out per lattice
+//     (meq_adjoint); lambda(t) = M^T nu + boundary terms, and
 //     dJ/ds_k += mu_k * (-(m_k - meq_k)).
+// Adjoint entries of solid nodes are zero and stay zero (never written).
 #include "sweep.cuh"
 
 namespace lbm {
-
-// ---- forward-mode dual numbers with four partials (rho, j_x, j_y, j_z) ----------
-template <class C>
-struct Dual4 {
-  C v, d[4];
-  __device__ __forceinline__ Dual4() {}
-  __device__ __forceinline__ Dual4(double x) : v(C(x)) { d[0] = d[1] = d[2] = d[3] = C(0); }
-  __device__ __forceinline__ static Dual4 var(C x, int k) {
-    Dual4 r(0.0);
-    r.v = x;
-    r.d[k] = C(1);
-    return r;
-  }
-};
-template <class C>
-__device__ __forceinline__ Dual4<C> operator+(const Dual4<C> &a, const Dual4<C> &b) {
-  Dual4<C> r;
-  r.v = a.v + b.v;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) r.d[k] = a.d[k] + b.d[k];
-  return r;
-}
-template <class C>
-__device__ __forceinline__ Dual4<C> operator-(const Dual4<C> &a, const Dual4<C> &b) {
-  Dual4<C> r;
-  r.v = a.v - b.v;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) r.d[k] = a.d[k] - b.d[k];
-  return r;
-}
-template <class C>
-__device__ __forceinline__ Dual4<C> operator-(const Dual4<C> &a) {
-  Dual4<C> r;
-  r.v = -a.v;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) r.d[k] = -a.d[k];
-  return r;
-}
-template <class C>
-__device__ __forceinline__ Dual4<C> operator*(const Dual4<C> &a, const Dual4<C> &b) {
-  Dual4<C> r;
-  r.v = a.v * b.v;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
-  return r;
-}
 
 namespace {
 
@@ -142,49 +97,110 @@ struct AdjGeo {
   const double *link_ephi;    // e_i . phi per link, i = opp(d)
   double *grad_q;             // accumulated dJ/dq per link
   double *grad_phi;           // accumulated dJ/dphi per link (3 each)
-  double *grad_s;             // accumulated dJ/ds_k (Q)
   double c0, c1, c2, b, rho0;
-  double s[19];               // relaxation rates
 };
+
+// sum_k smu_k * d meq_k / d(rho, j_x, j_y, j_z) for the equilibrium moments of
+// meq() (deviation form), smu_k = s_k mu_k on the non-conserved rows
+template <class C>
+__device__ __forceinline__ void meq_adjoint(D2Q9, const C (&smu)[9], C jx, C jy, C, C ir0,
+                                            C (&out)[4]) {
+  out[0] = C(-2) * smu[1] + smu[2];
+  const C a = C(6) * (smu[1] - smu[2]) * ir0;
+  out[1] = a * jx - smu[4] + (C(2) * smu[7] * jx + smu[8] * jy) * ir0;
+  out[2] = a * jy - smu[6] + (C(-2) * smu[7] * jy + smu[8] * jx) * ir0;
+  out[3] = C(0);
+}
+template <class C>
+__device__ __forceinline__ void meq_adjoint(D3Q19, const C (&smu)[19], C jx, C jy, C jz, C ir0,
+                                            C (&out)[4]) {
+  out[0] = C(-11) * smu[1] + C(3) * smu[2];
+  const C a = (C(38) * smu[1] - C(11) * smu[2]) * ir0;    // e, eps: 19 j^2, -5.5 j^2
+  const C px = (C(4) * smu[9] - C(2) * smu[10]) * ir0;    // 3p_xx, 3pi_xx along j_x
+  const C pyz = (C(-2) * smu[9] + smu[10]) * ir0;         // 3p_xx, 3pi_xx along j_y, j_z
+  const C w = (C(2) * smu[11] - smu[12]) * ir0;           // p_ww, pi_ww along j_y (-w along j_z)
+  const C c23 = C(2.0 / 3.0);
+  out[1] = (a + px) * jx - c23 * smu[4] + (smu[13] * jy + smu[15] * jz) * ir0;
+  out[2] = (a + pyz + w) * jy - c23 * smu[6] + (smu[13] * jx + smu[14] * jz) * ir0;
+  out[3] = (a + pyz - w) * jz - c23 * smu[8] + (smu[14] * jy + smu[15] * jx) * ir0;
+}
+
+// all moments of v in the pair form: m_k = sum_i M(k,i) v_i
+template <class L, class C>
+__device__ __forceinline__ void moments_all(const C (&v)[L::Q], C (&m)[L::Q]) {
+  constexpr int NP = L::NP;
+  C sp[NP], dp[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const int i = L::pair_first(p), ib = L::opp(i);
+    sp[p] = v[i] + v[ib];
+    dp[p] = v[i] - v[ib];
+  }
+#pragma unroll
+  for (int k = 0; k < L::Q; ++k) {
+    C acc = C(0);
+    if (Rows<L>::odd(k)) {
+#pragma unroll
+      for (int p = 0; p < NP; ++p) acc = madd(acc, L::M(k, L::pair_first(p)), dp[p]);
+    } else {
+      acc = madd(acc, L::M(k, 0), v[0]);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) acc = madd(acc, L::M(k, L::pair_first(p)), sp[p]);
+    }
+    m[k] = acc;
+  }
+}
 
 template <class L, class C>
 __global__ void __launch_bounds__(kAdjThreads)
     adjoint_step_kernel(const SweepArgs<C> sa, AuxArgs a, AdjGeo ag, const C *__restrict__ f,
-                        const C *__restrict__ lam_in, C *__restrict__ lam_out) {
+                        const C *__restrict__ lam_in, C *__restrict__ lam_out, double *gs_part) {
   constexpr int Q = L::Q;
+  constexpr int NP = L::NP;
   const long long N = a.N;
-  C gs[Q];
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  C gsum[Q];
 #pragma unroll
-  for (int k = 0; k < Q; ++k) gs[k] = C(0);
-  const LinkCoef<C> *coef = static_cast<const LinkCoef<C> *>(sa.geo.coef);
-  const C ir0 = sa.inv_rho0;
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-       n += (long long)gridDim.x * blockDim.x) {
-    const uint8_t cls = a.cls[n];
-    if (cls == kSolid) {
-#pragma unroll
-      for (int i = 0; i < Q; ++i) lam_out[(long long)i * N + n] = C(0);
-      continue;
+  for (int k = 0; k < Q; ++k) gsum[k] = C(0);
+  const uint8_t cls = n < N ? a.cls[n] : (uint8_t)kSolid;
+  if (cls != kSolid) {
+    int x, y, z;
+    if (N <= 0x7fffffffLL) {          // 32-bit index arithmetic whenever it fits
+      const unsigned nn = (unsigned)n, r = nn / (unsigned)a.nx;
+      x = (int)(nn - r * (unsigned)a.nx);
+      y = (int)(r % (unsigned)a.ny);
+      z = (int)(r / (unsigned)a.ny);
+    } else {
+      const long long r = n / a.nx;
+      x = (int)(n - r * a.nx);
+      y = (int)(r % a.ny);
+      z = (int)(r / a.ny);
     }
-    const int x = (int)(n % a.nx);
-    const long long r = n / a.nx;
-    const int y = (int)(r % a.ny), z = (int)(r / a.ny);
-    C g[Q], gp[Q], lp[Q], lpre[Q];
+    const C ir0 = sa.inv_rho0;
+    C g[Q], lp[Q], lpre[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       g[i] = f[(long long)i * N + n];
       lpre[i] = C(0);
     }
-    C drho;
-    collide<L, C>(g, gp, sa, drho);
-    // advection transpose: gather lambda_i(x + e_i) from fluid neighbours
+    // advection transpose: lambda'_i(x) = lambda_i(x + e_i); solid entries of the
+    // adjoint are kept at zero, so no class test is needed
+    const bool inside = x > 0 && x < a.nx - 1 && y > 0 && y < a.ny - 1 &&
+                        (L::D == 2 || (z > 0 && z < a.nz - 1));
+    const long long nxl = a.nx, nxy = (long long)a.nx * a.ny;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const long long nb = wrap_index(x, y, z, L::ex(i), L::ey(i), L::ez(i), a.nx, a.ny, a.nz, a.sy, a.sz);
-      lp[i] = a.cls[nb] != kSolid ? lam_in[(long long)i * N + nb] : C(0);
+      const long long nb = inside ? n + L::ex(i) + nxl * L::ey(i) + nxy * L::ez(i)
+                                  : wrap_index(x, y, z, L::ex(i), L::ey(i), L::ez(i), a.nx, a.ny,
+                                               a.nz, a.sy, a.sz);
+      lp[i] = lam_in[(long long)i * N + nb];
     }
     // boundary transpose and link gradients (Eq. 2.13)
     if (cls == kBoundary) {
+      C gp[Q];
+      C drho;
+      collide<L, C>(g, gp, sa, drho);
+      const LinkCoef<C> *coef = static_cast<const LinkCoef<C> *>(sa.geo.coef);
       const int bi = a.bidx[n];
       const uint32_t mask = a.bmask[bi];
       const int off = a.boff[bi];
@@ -217,75 +233,86 @@ __global__ void __launch_bounds__(kAdjThreads)
         }
       }
     }
-    // collision transpose
-    C drho_m = g[0];
-    C jx = C(0), jy = C(0), jz = C(0);
-#pragma unroll
-    for (int i = 1; i < Q; ++i) drho_m += g[i];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      jx = madd(jx, L::ex(i), g[i]);
-      jy = madd(jy, L::ey(i), g[i]);
-      jz = madd(jz, L::ez(i), g[i]);
-    }
-    const Dual4<C> dr = Dual4<C>::var(drho_m, 0), dx = Dual4<C>::var(jx, 1), dy = Dual4<C>::var(jy, 2),
-                   dz = Dual4<C>::var(jz, 3);
-    const Dual4<C> ir = Dual4<C>((double)ir0);
-    C mu[Q];
+    // collision transpose in moment space
+    C m[Q], mu[Q];
+    moments_all<L, C>(g, m);
+    moments_all<L, C>(lp, mu);
+    const C jx = m[3], jy = m[5], jz = L::D == 3 ? m[7] : C(0);
+    C smu[Q], nu[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
-      C m = C(0);
-#pragma unroll
-      for (int i = 0; i < Q; ++i) m = madd(m, L::M(k, i), lp[i]);
-      mu[k] = m * C(1.0 / row_norm2<L>(k));
+      if (Rows<L>::cons(k)) {
+        smu[k] = C(0);
+        mu[k] *= C(1.0 / row_norm2<L>(k));
+        continue;
+      }
+      smu[k] = sa.sn[k] * mu[k];                                      // s_k (M lambda')_k / |M_k|^2
+      mu[k] *= C(1.0 / row_norm2<L>(k));
+      gsum[k] = mu[k] * (meq(L{}, k, m[0], jx, jy, jz, ir0) - m[k]);   // d m'_k/d s_k
+      nu[k] = mu[k] - smu[k];                                         // (1 - s_k) mu_k
     }
-    C nu_c[4] = {mu[0], C(0), C(0), C(0)};    // rho, j_x, j_y, j_z rows
-    constexpr int jr[3] = {3, 5, 7};
-    nu_c[1] = mu[jr[0]];
-    nu_c[2] = mu[jr[1]];
-    if (L::D == 3) nu_c[3] = mu[jr[2]];
-    C nu[Q];
+    C dq[4];
+    meq_adjoint(L{}, smu, jx, jy, jz, ir0, dq);
+    nu[0] = mu[0] + dq[0];
+    nu[3] = mu[3] + dq[1];
+    nu[5] = mu[5] + dq[2];
+    if (L::D == 3) nu[7] = mu[7] + dq[3];
+    // lambda(t) = M^T nu + boundary terms, pair form
+    {
+      C e0 = lpre[0];
 #pragma unroll
-    for (int k = 0; k < Q; ++k) {
-      if (Rows<L>::cons(k)) { nu[k] = C(0); continue; }
-      const C sk = C(ag.s[k]);
-      const Dual4<C> me = meq(L{}, k, dr, dx, dy, dz, ir);
-      C mk = C(0);
-#pragma unroll
-      for (int i = 0; i < Q; ++i) mk = madd(mk, L::M(k, i), g[i]);
-      gs[k] += mu[k] * (me.v - mk);                  // d m'_k / d s_k = -(m_k - meq_k)
-      nu[k] = (C(1) - sk) * mu[k];
-      const C smu = sk * mu[k];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) nu_c[c] += smu * me.d[c];
+      for (int k = 0; k < Q; ++k)
+        if (!Rows<L>::odd(k)) e0 = madd(e0, L::M(k, 0), nu[k]);
+      lam_out[n] = e0;
     }
-    nu[0] = nu_c[0];
-    nu[jr[0]] = nu_c[1];
-    nu[jr[1]] = nu_c[2];
-    if (L::D == 3) nu[jr[2]] = nu_c[3];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      C v = lpre[i];
+    for (int p = 0; p < NP; ++p) {
+      const int i = L::pair_first(p), ib = L::opp(i);
+      C ev = C(0), od = C(0);
 #pragma unroll
-      for (int k = 0; k < Q; ++k) v = madd(v, L::M(k, i), nu[k]);
-      lam_out[(long long)i * N + n] = v;
+      for (int k = 0; k < Q; ++k) {
+        if (Rows<L>::odd(k)) od = madd(od, L::M(k, i), nu[k]);
+        else ev = madd(ev, L::M(k, i), nu[k]);
+      }
+      lam_out[(long long)i * N + n] = lpre[i] + ev + od;
+      lam_out[(long long)ib * N + n] = lpre[ib] + ev - od;
     }
   }
-  // dJ/ds: block reduction, then one FP64 atomic per row and block
-  __shared__ double sh[kAdjThreads / 32][Q];
+  // dJ/ds: block sums in the compute type (FP64 arithmetic is slow on this GPU),
+  // added in FP64 to this block's own partial record (no atomics)
+  __shared__ C sh[kAdjThreads / 32][Q];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
-    double v = (double)gs[k];
+    C v = gsum[k];
+    if (Rows<L>::cons(k)) continue;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if (lane == 0) sh[warp][k] = v;
   }
   __syncthreads();
-  if (threadIdx.x < Q) {
-    double v = 0.0;
+  if (threadIdx.x < Q && !Rows<L>::cons(threadIdx.x)) {
+    C v = C(0);
     for (int w = 0; w < kAdjThreads / 32; ++w) v += sh[w][threadIdx.x];
-    atomic_add_double(ag.grad_s + threadIdx.x, v);
+    gs_part[(long long)blockIdx.x * Q + threadIdx.x] += (double)v;
   }
+}
+
+// sum of the per-block partial records: grad_s[k] = sum_b part[b*Q + k]; block k
+// sums row k with a fixed order (deterministic)
+template <int Q>
+__global__ void __launch_bounds__(256) gs_finish_kernel(const double *part, long long n_blocks,
+                                                        double *grad_s) {
+  const int k = blockIdx.x;
+  double v = 0.0;
+  for (long long b = threadIdx.x; b < n_blocks; b += blockDim.x) v += part[b * Q + k];
+  __shared__ double sh[256];
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) grad_s[k] = sh[0];
 }
 
 int adj_blocks(long long N) {
@@ -340,23 +367,32 @@ cudaError_t launch_loss(int lattice, int precision, const AuxArgs &a, const void
 cudaError_t launch_adjoint_step(int lattice, int precision, const SweepArgs<double> &a64,
                                 const SweepArgs<float> &a32, const AuxArgs &a, const double *link_q,
                                 const double *link_ephi, double *grad_q, double *grad_phi,
-                                double *grad_s, double c0, double c1, double c2, double b,
-                                double rho0, const double *s, const void *f, const void *lam_in,
-                                void *lam_out, cudaStream_t st) {
-  AdjGeo ag{link_q, link_ephi, grad_q, grad_phi, grad_s, c0, c1, c2, b, rho0, {0}};
-  for (int k = 0; k < 19; ++k) ag.s[k] = s[k];
+                                double c0, double c1, double c2, double b, double rho0,
+                                const void *f, const void *lam_in, void *lam_out,
+                                double *gs_part, cudaStream_t st) {
+  AdjGeo ag{link_q, link_ephi, grad_q, grad_phi, c0, c1, c2, b, rho0};
+  const unsigned blocks = (unsigned)adjoint_partial_blocks(a.N);
   return with_lattice(lattice, [&](auto lat) {
     using L = decltype(lat);
     if (precision == 0)
-      adjoint_step_kernel<L, double><<<adj_blocks(a.N), kAdjThreads, 0, st>>>(
+      adjoint_step_kernel<L, double><<<blocks, kAdjThreads, 0, st>>>(
           a64, a, ag, static_cast<const double *>(f), static_cast<const double *>(lam_in),
-          static_cast<double *>(lam_out));
+          static_cast<double *>(lam_out), gs_part);
     else
-      adjoint_step_kernel<L, float><<<adj_blocks(a.N), kAdjThreads, 0, st>>>(
+      adjoint_step_kernel<L, float><<<blocks, kAdjThreads, 0, st>>>(
           a32, a, ag, static_cast<const float *>(f), static_cast<const float *>(lam_in),
-          static_cast<float *>(lam_out));
+          static_cast<float *>(lam_out), gs_part);
     return cudaGetLastError();
   });
+}
+
+long long adjoint_partial_blocks(long long N) { return (N + kAdjThreads - 1) / kAdjThreads; }
+
+cudaError_t launch_adjoint_finish(int lattice, const double *gs_part, long long n_blocks,
+                                  double *grad_s, cudaStream_t st) {
+  if (lattice == 0) gs_finish_kernel<9><<<9, 256, 0, st>>>(gs_part, n_blocks, grad_s);
+  else gs_finish_kernel<19><<<19, 256, 0, st>>>(gs_part, n_blocks, grad_s);
+  return cudaGetLastError();
 }
 
 }  // namespace lbm

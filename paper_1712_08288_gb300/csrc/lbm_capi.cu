@@ -798,11 +798,15 @@ int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *ma
   char *ck = nullptr, *seg = nullptr, *fin = nullptr, *lam0 = nullptr, *lam1 = nullptr;
   uint8_t *dmask = nullptr;
   double *dut = nullptr, *dgs = nullptr, *dgq = nullptr, *dgp = nullptr, *dJ = nullptr;
+  double *gpart = nullptr;
+  const long long pblocks = adjoint_partial_blocks(c->N);
   std::vector<long long> tck(nseg);
   int rc = LBM_OK;
   auto cleanup = [&]() {
     cudaFree(ck); cudaFree(seg); cudaFree(fin); cudaFree(lam0); cudaFree(lam1); cudaFree(dmask);
-    cudaFree(dut); cudaFree(dgs); cudaFree(dgq); cudaFree(dgp); cudaFree(dJ);
+    cudaFree(dut); cudaFree(dgs); cudaFree(dgq); cudaFree(dgp); cudaFree(dJ); cudaFree(gpart);
+    c->a64.save = nullptr;
+    c->a32.save = nullptr;
   };
 #define ADJ_CUDA(call)                                                                      \
   do {                                                                                      \
@@ -824,7 +828,10 @@ int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *ma
   ADJ_CUDA(cudaMalloc((void **)&dgq, sizeof(double) * std::max<long long>(1, nl)));
   ADJ_CUDA(cudaMalloc((void **)&dgp, sizeof(double) * 3 * std::max<long long>(1, nl)));
   ADJ_CUDA(cudaMalloc((void **)&dJ, sizeof(double)));
+  ADJ_CUDA(cudaMalloc((void **)&gpart, sizeof(double) * c->Q * pblocks));
   cudaStream_t st = c->stream;
+  ADJ_CUDA(cudaMemsetAsync(gpart, 0, sizeof(double) * c->Q * pblocks, st));
+  ADJ_CUDA(cudaMemsetAsync(lam1, 0, state, st));        // solid entries stay zero
   ADJ_CUDA(cudaMemcpyAsync(dmask, mask, c->N, cudaMemcpyHostToDevice, st));
   ADJ_CUDA(cudaMemcpyAsync(dut, u_target, sizeof(double) * c->N * c->D, cudaMemcpyHostToDevice, st));
   ADJ_CUDA(cudaMemsetAsync(dgs, 0, sizeof(double) * 19, st));
@@ -860,17 +867,22 @@ int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *ma
     c->t = tck[sgm];
     const int len = (int)std::min(K, T - sgm * K);
     for (int r = 0; r < len; ++r) {
-      ADJ_CUDA(launch_export_state(c->lattice, c->precision, aux_args(c), (c->t & 1) != 0,
-                                   seg + state * r, st));
-      if ((rc = lbm_step(c, 1)) != LBM_OK) { cleanup(); return rc; }
+      // the recomputing sweep also writes the pre-collision state of step r
+      if (c->precision == LBM_F64) c->a64.save = reinterpret_cast<double *>(seg + state * r);
+      else c->a32.save = reinterpret_cast<float *>(seg + state * r);
+      rc = lbm_step(c, 1);
+      c->a64.save = nullptr;
+      c->a32.save = nullptr;
+      if (rc != LBM_OK) { cleanup(); return rc; }
     }
     for (int r = len - 1; r >= 0; --r) {
       ADJ_CUDA(launch_adjoint_step(c->lattice, c->precision, c->a64, c->a32, aux_args(c),
-                                   c->dev_link_q, c->dev_link_ephi, dgq, dgp, dgs, c->c0, c->c1,
-                                   c->c2, c->b, c->rho0, c->s, seg + state * r, lin, lout, st));
+                                   c->dev_link_q, c->dev_link_ephi, dgq, dgp, c->c0, c->c1, c->c2,
+                                   c->b, c->rho0, seg + state * r, lin, lout, gpart, st));
       std::swap(lin, lout);
     }
   }
+  ADJ_CUDA(launch_adjoint_finish(c->lattice, gpart, pblocks, dgs, st));
   // back to the state after the forward run
   ADJ_CUDA(load_raw(fin));
   c->t = t0 + T;

@@ -86,6 +86,9 @@ struct SweepArgs {
   // the node itself, odd step slot i of x + e_i (no wrap)
   long long koff_even[19];
   long long koff_odd[19];
+  // when non-null, the sweep also writes every fluid node's pre-collision
+  // deviations g_i(x, t) here, natural layout save[i*N + n] (adjoint recomputation)
+  C *save = nullptr;
 };
 
 // launchers (return cudaGetLastError() of the launch)
@@ -140,9 +143,13 @@ cudaError_t launch_loss(int lattice, int precision, const AuxArgs &a, const void
 cudaError_t launch_adjoint_step(int lattice, int precision, const SweepArgs<double> &a64,
                                 const SweepArgs<float> &a32, const AuxArgs &a, const double *link_q,
                                 const double *link_ephi, double *grad_q, double *grad_phi,
-                                double *grad_s, double c0, double c1, double c2, double b,
-                                double rho0, const double *s, const void *f, const void *lam_in,
-                                void *lam_out, cudaStream_t st);
+                                double c0, double c1, double c2, double b, double rho0,
+                                const void *f, const void *lam_in, void *lam_out,
+                                double *gs_part, cudaStream_t st);
+// per-block partial sums of dJ/ds (Q doubles per block), reduced by launch_adjoint_finish
+long long adjoint_partial_blocks(long long N);
+cudaError_t launch_adjoint_finish(int lattice, const double *gs_part, long long n_blocks,
+                                  double *grad_s, cudaStream_t st);
 int norm_blocks_for(long long N);
 
 }  // namespace lbm

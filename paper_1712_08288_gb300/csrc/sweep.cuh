@@ -504,6 +504,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
           g[L::opp(dd)] = Storage<T>::load(lnk + boff + __popc(bmask & ((1u << dd) - 1u)));
     }
 
+    if (A.save) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) A.save[(long long)i * A.N + n] = g[i];
+    }
+
     C gp[Q];
     C drho;
     collide<L, C>(g, gp, A, drho);
