@@ -31,6 +31,10 @@ namespace lbm {
 namespace {
 
 constexpr int kAdjThreads = 128;
+// resident blocks per SM the FP32 adjoint step is compiled for (register budget)
+#ifndef LBM_ADJ_MINB_F32
+#define LBM_ADJ_MINB_F32 6
+#endif
 
 __device__ __forceinline__ void atomic_add_double(double *p, double v) { atomicAdd(p, v); }
 
@@ -92,13 +96,50 @@ __global__ void loss_kernel(AuxArgs a, const C *g, const uint8_t *mask, const do
   if ((threadIdx.x & 31) == 0) atomic_add_double(J, acc);
 }
 
+// Link data of the adjoint step.  The gradients with respect to a link's wall
+// fraction q and wall velocity phi are linear in two sums over the steps
+// (Eq. 2.13 differentiated through l(q)):
+//   dJ/dq   = b sum_t lambda_i (A' f_d + B' f'_i + C' f'_d) + b W' sum_t lambda_i,
+//   dJ/dphi = b 2 w_i rho0 e_i / ((1 + l) c_s^2) sum_t lambda_i,
+// with ' = d/dq.  The kernel accumulates only sum_t lambda_i and the first sum, per
+// link and in the compute type; the host folds in the other factors in FP64.
 struct AdjGeo {
-  const double *link_q;       // wall fraction per link (device order)
-  const double *link_ephi;    // e_i . phi per link, i = opp(d)
-  double *grad_q;             // accumulated dJ/dq per link
-  double *grad_phi;           // accumulated dJ/dphi per link (3 each)
-  double c0, c1, c2, b, rho0;
+  const void *dcoef;          // LinkCoef<C> per link: (A', B', C', 0)
+  void *acc;                  // 2 C per link: sum lambda_i, sum lambda_i (A' g_d + B' g'_i + C' g'_d)
 };
+
+// position of row k among the non-conserved rows
+template <class L>
+__host__ __device__ constexpr int nc_slot(int k) {
+  int s = 0;
+  for (int r = 0; r < k; ++r)
+    if (!L::conserved(r)) ++s;
+  return s;
+}
+static_assert(nc_slot<D3Q19>(19) <= 16 && nc_slot<D2Q9>(9) <= 16, "at most 16 relaxed rows");
+
+// Transposing warp reduction of 16 values per lane: at each of the offsets 16, 8,
+// 4, 2 a lane keeps the half of its values that its lane bit selects and adds the
+// partner's copy of that half; the pair (l, l^1) is combined last.  Lane l returns
+// the warp sum of v[l >> 1]: 16 shuffles instead of 16 x 5.
+template <class C>
+__device__ __forceinline__ C warp_sum16(const C (&v)[16]) {
+  const unsigned lane = threadIdx.x & 31u;
+  const bool b4 = lane & 16u, b3 = lane & 8u, b2 = lane & 4u, b1 = lane & 2u;
+  C a8[8], a4[4], a2[2];
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    a8[j] = (b4 ? v[j + 8] : v[j]) + __shfl_xor_sync(0xffffffffu, b4 ? v[j] : v[j + 8], 16);
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    a4[j] = (b3 ? a8[j + 4] : a8[j]) + __shfl_xor_sync(0xffffffffu, b3 ? a8[j] : a8[j + 4], 8);
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+    a2[j] = (b2 ? a4[j + 2] : a4[j]) + __shfl_xor_sync(0xffffffffu, b2 ? a4[j] : a4[j + 2], 4);
+  C r = (b1 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, b1 ? a2[0] : a2[1], 2);
+  r += __shfl_xor_sync(0xffffffffu, r, 1);
+  return r;
+}
 
 // sum_k smu_k * d meq_k / d(rho, j_x, j_y, j_z) for the equilibrium moments of
 // meq() (deviation form), smu_k = s_k mu_k on the non-conserved rows
@@ -151,8 +192,11 @@ __device__ __forceinline__ void moments_all(const C (&v)[L::Q], C (&m)[L::Q]) {
   }
 }
 
-template <class L, class C>
-__global__ void __launch_bounds__(kAdjThreads)
+// One step back in time, one node per thread.  SMALL: node indices fit in 31 bits,
+// so neighbour indices come from the node's wrapped coordinates in 32-bit
+// arithmetic.
+template <class L, class C, bool SMALL>
+__global__ void __launch_bounds__(kAdjThreads, sizeof(C) == 4 ? LBM_ADJ_MINB_F32 : 3)
     adjoint_step_kernel(const SweepArgs<C> sa, AuxArgs a, AdjGeo ag, const C *__restrict__ f,
                         const C *__restrict__ lam_in, C *__restrict__ lam_out, double *gs_part) {
   constexpr int Q = L::Q;
@@ -165,12 +209,7 @@ __global__ void __launch_bounds__(kAdjThreads)
   const uint8_t cls = n < N ? a.cls[n] : (uint8_t)kSolid;
   if (cls != kSolid) {
     int x, y, z;
-    if (N <= 0x7fffffffLL) {          // 32-bit index arithmetic whenever it fits
-      const unsigned nn = (unsigned)n, r = nn / (unsigned)a.nx;
-      x = (int)(nn - r * (unsigned)a.nx);
-      y = (int)(r % (unsigned)a.ny);
-      z = (int)(r / (unsigned)a.ny);
-    } else {
+    {
       const long long r = n / a.nx;
       x = (int)(n - r * a.nx);
       y = (int)(r % a.ny);
@@ -184,16 +223,17 @@ __global__ void __launch_bounds__(kAdjThreads)
       lpre[i] = C(0);
     }
     // advection transpose: lambda'_i(x) = lambda_i(x + e_i); solid entries of the
-    // adjoint are kept at zero, so no class test is needed
-    const bool inside = x > 0 && x < a.nx - 1 && y > 0 && y < a.ny - 1 &&
-                        (L::D == 2 || (z > 0 && z < a.nz - 1));
-    const long long nxl = a.nx, nxy = (long long)a.nx * a.ny;
+    // adjoint are kept at zero, so no class test is needed.  Neighbours follow the
+    // periodic wrap, skewed along x by (sy, sz).
+    if constexpr (SMALL) {
+      const Neighbours<L, true> nb(x, y, z, a.nx, a.ny, a.nz, a.sy, a.sz);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const long long nb = inside ? n + L::ex(i) + nxl * L::ey(i) + nxy * L::ez(i)
-                                  : wrap_index(x, y, z, L::ex(i), L::ey(i), L::ez(i), a.nx, a.ny,
-                                               a.nz, a.sy, a.sz);
-      lp[i] = lam_in[(long long)i * N + nb];
+      for (int i = 0; i < Q; ++i) lp[i] = lam_in[(long long)i * N + nb(i)];
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+        lp[i] = lam_in[(long long)i * N + wrap_index(x, y, z, L::ex(i), L::ey(i), L::ez(i), a.nx,
+                                                     a.ny, a.nz, a.sy, a.sz)];
     }
     // boundary transpose and link gradients (Eq. 2.13)
     if (cls == kBoundary) {
@@ -215,21 +255,11 @@ __global__ void __launch_bounds__(kAdjThreads)
           lp[dd] += c.c * av;
           lpre[i] += sa.one_minus_b * av;
           lpre[dd] += c.a * av;
-          const double q = ag.link_q[k];
-          const double l = ag.c0 + ag.c1 * q + ag.c2 * q * q;
-          const double lq = ag.c1 + 2.0 * ag.c2 * q;
-          const double inv = 1.0 / (1.0 + l), inv2 = inv * inv;
-          const double dA = (-2.0 * (1.0 + l) + 2.0 * q * lq) * inv2;
-          const double dB = lq * inv2;
-          const double dC = (2.0 * (1.0 + l) - lq - 2.0 * q * lq) * inv2;
-          const double E = L::w(i) * ag.rho0 * 3.0 * ag.link_ephi[k];   // w rho0 e.phi / c_s^2
-          const double dW = -2.0 * lq * inv2 * E;
-          const double da = (double)av * ag.b;
-          ag.grad_q[k] += da * (dA * (double)g[dd] + dB * (double)gp[i] + dC * (double)gp[dd] + dW);
-          const double wphi = da * 2.0 * inv * L::w(i) * ag.rho0 * 3.0;
-          ag.grad_phi[3 * k + 0] += wphi * L::ex(i);
-          ag.grad_phi[3 * k + 1] += wphi * L::ey(i);
-          ag.grad_phi[3 * k + 2] += wphi * L::ez(i);
+          // deviations suffice: A' + B' + C' = 0 removes the w_i rho0 parts
+          const LinkCoef<C> dc = static_cast<const LinkCoef<C> *>(ag.dcoef)[k];
+          C *acc = static_cast<C *>(ag.acc) + 2 * (long long)k;
+          acc[0] += av;
+          acc[1] += av * (dc.a * g[dd] + dc.bb * gp[i] + dc.c * gp[dd]);
         }
       }
     }
@@ -280,20 +310,35 @@ __global__ void __launch_bounds__(kAdjThreads)
   }
   // dJ/ds: block sums in the compute type (FP64 arithmetic is slow on this GPU),
   // added in FP64 to this block's own partial record (no atomics)
-  __shared__ C sh[kAdjThreads / 32][Q];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  C v[16];
 #pragma unroll
-  for (int k = 0; k < Q; ++k) {
-    C v = gsum[k];
-    if (Rows<L>::cons(k)) continue;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[warp][k] = v;
-  }
+  for (int j = 0; j < 16; ++j) v[j] = C(0);
+#pragma unroll
+  for (int k = 0; k < Q; ++k)
+    if (!Rows<L>::cons(k)) v[nc_slot<L>(k)] = gsum[k];
+  const C wsum = warp_sum16(v);
+  __shared__ C sh[kAdjThreads / 32][16];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if ((lane & 1) == 0) sh[warp][lane >> 1] = wsum;
   __syncthreads();
   if (threadIdx.x < Q && !Rows<L>::cons(threadIdx.x)) {
-    C v = C(0);
-    for (int w = 0; w < kAdjThreads / 32; ++w) v += sh[w][threadIdx.x];
-    gs_part[(long long)blockIdx.x * Q + threadIdx.x] += (double)v;
+    int slot = 0;
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+      if (k == (int)threadIdx.x) slot = nc_slot<L>(k);
+    C t = C(0);
+    for (int w = 0; w < kAdjThreads / 32; ++w) t += sh[w][slot];
+    gs_part[(long long)blockIdx.x * Q + threadIdx.x] += (double)t;
+  }
+}
+
+// add the per-link sums of one segment to the FP64 totals and clear them
+template <class C>
+__global__ void link_flush_kernel(C *acc, double *tot, long long n) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x) {
+    tot[j] += (double)acc[j];
+    acc[j] = C(0);
   }
 }
 
@@ -365,25 +410,40 @@ cudaError_t launch_loss(int lattice, int precision, const AuxArgs &a, const void
 }
 
 cudaError_t launch_adjoint_step(int lattice, int precision, const SweepArgs<double> &a64,
-                                const SweepArgs<float> &a32, const AuxArgs &a, const double *link_q,
-                                const double *link_ephi, double *grad_q, double *grad_phi,
-                                double c0, double c1, double c2, double b, double rho0,
-                                const void *f, const void *lam_in, void *lam_out,
+                                const SweepArgs<float> &a32, const AuxArgs &a, const void *dcoef,
+                                void *link_acc, const void *f, const void *lam_in, void *lam_out,
                                 double *gs_part, cudaStream_t st) {
-  AdjGeo ag{link_q, link_ephi, grad_q, grad_phi, c0, c1, c2, b, rho0};
+  const AdjGeo ag{dcoef, link_acc};
   const unsigned blocks = (unsigned)adjoint_partial_blocks(a.N);
+  const bool small = a.N < (1LL << 31);
   return with_lattice(lattice, [&](auto lat) {
     using L = decltype(lat);
-    if (precision == 0)
-      adjoint_step_kernel<L, double><<<blocks, kAdjThreads, 0, st>>>(
-          a64, a, ag, static_cast<const double *>(f), static_cast<const double *>(lam_in),
-          static_cast<double *>(lam_out), gs_part);
-    else
-      adjoint_step_kernel<L, float><<<blocks, kAdjThreads, 0, st>>>(
-          a32, a, ag, static_cast<const float *>(f), static_cast<const float *>(lam_in),
-          static_cast<float *>(lam_out), gs_part);
+    auto go = [&](const auto &sa, auto sm) {
+      using C = std::remove_cv_t<std::remove_reference_t<decltype(sa.inv_rho0)>>;
+      adjoint_step_kernel<L, C, decltype(sm)::value><<<blocks, kAdjThreads, 0, st>>>(
+          sa, a, ag, static_cast<const C *>(f), static_cast<const C *>(lam_in),
+          static_cast<C *>(lam_out), gs_part);
+    };
+    if (precision == 0) {
+      if (small) go(a64, std::true_type{});
+      else go(a64, std::false_type{});
+    } else {
+      if (small) go(a32, std::true_type{});
+      else go(a32, std::false_type{});
+    }
     return cudaGetLastError();
   });
+}
+
+cudaError_t launch_link_flush(int precision, void *link_acc, double *tot, long long n,
+                              cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 8);
+  if (precision == 0)
+    link_flush_kernel<double><<<blocks, 256, 0, st>>>(static_cast<double *>(link_acc), tot, n);
+  else
+    link_flush_kernel<float><<<blocks, 256, 0, st>>>(static_cast<float *>(link_acc), tot, n);
+  return cudaGetLastError();
 }
 
 long long adjoint_partial_blocks(long long N) { return (N + kAdjThreads - 1) / kAdjThreads; }

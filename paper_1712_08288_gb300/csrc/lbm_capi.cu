@@ -78,8 +78,6 @@ struct lbm_ctx {
   std::vector<double> link_q;
   std::vector<double> link_uw;  // 3 per link
   std::vector<int64_t> link_src; // input position of the link at each device position
-  double *dev_link_q = nullptr;    // wall fraction per link (adjoint)
-  double *dev_link_ephi = nullptr; // e_i . phi per link (adjoint)
   long long n_links = 0, n_fluid = 0, n_boundary = 0;
 
   SweepArgs<double> a64;
@@ -227,22 +225,6 @@ static int upload_coefficients(lbm_ctx *c) {
     }
     return 0;
   });
-  {
-    std::vector<double> ephi(nl);
-    with_lat(c->lattice, [&](auto lat) {
-      using L = decltype(lat);
-      for (long long k = 0; k < nl; ++k) {
-        const int i = L::opp(c->link_dir[k]);
-        ephi[k] = L::ex(i) * c->link_uw[3 * k] + L::ey(i) * c->link_uw[3 * k + 1] +
-                  L::ez(i) * c->link_uw[3 * k + 2];
-      }
-      return 0;
-    });
-    if (!c->dev_link_q) CUDA_OR_FAIL(c, cudaMalloc((void **)&c->dev_link_q, sizeof(double) * nl));
-    if (!c->dev_link_ephi) CUDA_OR_FAIL(c, cudaMalloc((void **)&c->dev_link_ephi, sizeof(double) * nl));
-    CUDA_OR_FAIL(c, cudaMemcpy(c->dev_link_q, c->link_q.data(), sizeof(double) * nl, cudaMemcpyHostToDevice));
-    CUDA_OR_FAIL(c, cudaMemcpy(c->dev_link_ephi, ephi.data(), sizeof(double) * nl, cudaMemcpyHostToDevice));
-  }
   if (c->precision == LBM_F64) {
     CUDA_OR_FAIL(c, cudaMemcpy(c->coef, co.data(), sizeof(double) * co.size(),
                                cudaMemcpyHostToDevice));
@@ -260,8 +242,6 @@ static void free_geometry(lbm_ctx *c) {
   cudaFree(c->boff); c->boff = nullptr;
   cudaFree(c->coef); c->coef = nullptr;
   cudaFree(c->lnk); c->lnk = nullptr;
-  cudaFree(c->dev_link_q); c->dev_link_q = nullptr;
-  cudaFree(c->dev_link_ephi); c->dev_link_ephi = nullptr;
 }
 
 // Tile descriptors (see TileDesc) of every run of kTileW nodes along x that holds
@@ -797,14 +777,16 @@ int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *ma
   const long long nl = c->n_links;
   char *ck = nullptr, *seg = nullptr, *fin = nullptr, *lam0 = nullptr, *lam1 = nullptr;
   uint8_t *dmask = nullptr;
-  double *dut = nullptr, *dgs = nullptr, *dgq = nullptr, *dgp = nullptr, *dJ = nullptr;
+  double *dut = nullptr, *dgs = nullptr, *dtot = nullptr, *dJ = nullptr;
   double *gpart = nullptr;
+  void *dcoef = nullptr, *acc = nullptr;
   const long long pblocks = adjoint_partial_blocks(c->N);
   std::vector<long long> tck(nseg);
   int rc = LBM_OK;
   auto cleanup = [&]() {
     cudaFree(ck); cudaFree(seg); cudaFree(fin); cudaFree(lam0); cudaFree(lam1); cudaFree(dmask);
-    cudaFree(dut); cudaFree(dgs); cudaFree(dgq); cudaFree(dgp); cudaFree(dJ); cudaFree(gpart);
+    cudaFree(dut); cudaFree(dgs); cudaFree(dtot); cudaFree(dJ); cudaFree(gpart);
+    cudaFree(dcoef); cudaFree(acc);
     c->a64.save = nullptr;
     c->a32.save = nullptr;
   };
@@ -825,8 +807,10 @@ int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *ma
   ADJ_CUDA(cudaMalloc((void **)&dmask, c->N));
   ADJ_CUDA(cudaMalloc((void **)&dut, sizeof(double) * c->N * c->D));
   ADJ_CUDA(cudaMalloc((void **)&dgs, sizeof(double) * 19));
-  ADJ_CUDA(cudaMalloc((void **)&dgq, sizeof(double) * std::max<long long>(1, nl)));
-  ADJ_CUDA(cudaMalloc((void **)&dgp, sizeof(double) * 3 * std::max<long long>(1, nl)));
+  const long long nl1 = std::max<long long>(1, nl);
+  ADJ_CUDA(cudaMalloc((void **)&dtot, sizeof(double) * 2 * nl1));
+  ADJ_CUDA(cudaMalloc(&acc, csize * 2 * nl1));
+  ADJ_CUDA(cudaMalloc(&dcoef, csize * 4 * nl1));
   ADJ_CUDA(cudaMalloc((void **)&dJ, sizeof(double)));
   ADJ_CUDA(cudaMalloc((void **)&gpart, sizeof(double) * c->Q * pblocks));
   cudaStream_t st = c->stream;
@@ -835,8 +819,24 @@ int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *ma
   ADJ_CUDA(cudaMemcpyAsync(dmask, mask, c->N, cudaMemcpyHostToDevice, st));
   ADJ_CUDA(cudaMemcpyAsync(dut, u_target, sizeof(double) * c->N * c->D, cudaMemcpyHostToDevice, st));
   ADJ_CUDA(cudaMemsetAsync(dgs, 0, sizeof(double) * 19, st));
-  ADJ_CUDA(cudaMemsetAsync(dgq, 0, sizeof(double) * std::max<long long>(1, nl), st));
-  ADJ_CUDA(cudaMemsetAsync(dgp, 0, sizeof(double) * 3 * std::max<long long>(1, nl), st));
+  ADJ_CUDA(cudaMemsetAsync(dtot, 0, sizeof(double) * 2 * nl1, st));
+  ADJ_CUDA(cudaMemsetAsync(acc, 0, csize * 2 * nl1, st));
+  // d(A, B, C)/dq per link (Eq. 2.10 with l = c0 + c1 q + c2 q^2), device order
+  std::vector<double> hdc(4 * nl1, 0.0);
+  for (long long k = 0; k < nl; ++k) {
+    const double q = c->link_q[k], l = l_of(c, q), dl = c->c1 + 2.0 * c->c2 * q;
+    const double inv2 = 1.0 / ((1.0 + l) * (1.0 + l));
+    hdc[4 * k + 0] = (2.0 * q * dl - 2.0 * (1.0 + l)) * inv2;
+    hdc[4 * k + 1] = dl * inv2;
+    hdc[4 * k + 2] = (2.0 * (1.0 + l) - dl - 2.0 * q * dl) * inv2;
+  }
+  if (c->precision == LBM_F64) {
+    ADJ_CUDA(cudaMemcpyAsync(dcoef, hdc.data(), sizeof(double) * hdc.size(), cudaMemcpyHostToDevice, st));
+  } else {
+    std::vector<float> fdc(hdc.begin(), hdc.end());
+    ADJ_CUDA(cudaMemcpyAsync(dcoef, fdc.data(), sizeof(float) * fdc.size(), cudaMemcpyHostToDevice, st));
+    ADJ_CUDA(cudaStreamSynchronize(st));     // fdc is about to go out of scope
+  }
   ADJ_CUDA(cudaMemsetAsync(dJ, 0, sizeof(double), st));
   auto save_raw = [&](char *dst) -> cudaError_t {
     cudaError_t e = cudaMemcpyAsync(dst, c->pop_alloc, raw_pop, cudaMemcpyDeviceToDevice, st);
@@ -876,24 +876,22 @@ int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *ma
       if (rc != LBM_OK) { cleanup(); return rc; }
     }
     for (int r = len - 1; r >= 0; --r) {
-      ADJ_CUDA(launch_adjoint_step(c->lattice, c->precision, c->a64, c->a32, aux_args(c),
-                                   c->dev_link_q, c->dev_link_ephi, dgq, dgp, c->c0, c->c1, c->c2,
-                                   c->b, c->rho0, seg + state * r, lin, lout, gpart, st));
+      ADJ_CUDA(launch_adjoint_step(c->lattice, c->precision, c->a64, c->a32, aux_args(c), dcoef,
+                                   acc, seg + state * r, lin, lout, gpart, st));
       std::swap(lin, lout);
     }
+    ADJ_CUDA(launch_link_flush(c->precision, acc, dtot, 2 * nl, st));
   }
   ADJ_CUDA(launch_adjoint_finish(c->lattice, gpart, pblocks, dgs, st));
   // back to the state after the forward run
   ADJ_CUDA(load_raw(fin));
   c->t = t0 + T;
   double hJ = 0.0;
-  std::vector<double> hgs(19), hgq(nl), hgp(3 * nl);
+  std::vector<double> hgs(19), htot(2 * nl);
   ADJ_CUDA(cudaMemcpyAsync(&hJ, dJ, sizeof(double), cudaMemcpyDeviceToHost, st));
   ADJ_CUDA(cudaMemcpyAsync(hgs.data(), dgs, sizeof(double) * 19, cudaMemcpyDeviceToHost, st));
-  if (nl) {
-    ADJ_CUDA(cudaMemcpyAsync(hgq.data(), dgq, sizeof(double) * nl, cudaMemcpyDeviceToHost, st));
-    ADJ_CUDA(cudaMemcpyAsync(hgp.data(), dgp, sizeof(double) * 3 * nl, cudaMemcpyDeviceToHost, st));
-  }
+  if (nl)
+    ADJ_CUDA(cudaMemcpyAsync(htot.data(), dtot, sizeof(double) * 2 * nl, cudaMemcpyDeviceToHost, st));
   ADJ_CUDA(cudaStreamSynchronize(st));
   cleanup();
 #undef ADJ_CUDA
@@ -903,12 +901,29 @@ int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *ma
       using L = decltype(lat);
       return L::conserved(k) ? 0.0 : hgs[k];
     });
-  for (long long pos = 0; pos < nl; ++pos) {
-    const long long k = c->link_src[pos];
-    if (grad_q) grad_q[k] = hgq[pos];
-    if (grad_uw)
-      for (int a = 0; a < 3; ++a) grad_uw[3 * k + a] = (a < c->D) ? hgp[3 * pos + a] : 0.0;
-  }
+  // fold in the q- and phi-dependent factors: W = 2 w_i rho0 e_i.phi / ((1 + l) c_s^2)
+  // of Eq. 2.13 with c_s^2 = 1/3, so W' = -2 w_i rho0 3 e_i.phi l' / (1 + l)^2
+  with_lat(c->lattice, [&](auto lat) {
+    using L = decltype(lat);
+    for (long long pos = 0; pos < nl; ++pos) {
+      const long long k = c->link_src[pos];
+      const int i = L::opp(c->link_dir[pos]);
+      const double q = c->link_q[pos], l = l_of(c, q), dl = c->c1 + 2.0 * c->c2 * q;
+      const double inv = 1.0 / (1.0 + l);
+      const double ephi = L::ex(i) * c->link_uw[3 * pos] + L::ey(i) * c->link_uw[3 * pos + 1] +
+                          L::ez(i) * c->link_uw[3 * pos + 2];
+      const double wr = 2.0 * L::w(i) * c->rho0 * 3.0;
+      const double dW = -wr * ephi * dl * inv * inv;
+      const double s_lam = htot[2 * pos], s_q = htot[2 * pos + 1];
+      if (grad_q) grad_q[k] = c->b * (s_q + dW * s_lam);
+      if (grad_uw) {
+        const int e[3] = {L::ex(i), L::ey(i), L::ez(i)};
+        for (int a = 0; a < 3; ++a)
+          grad_uw[3 * k + a] = (a < c->D) ? c->b * wr * inv * e[a] * s_lam : 0.0;
+      }
+    }
+    return 0;
+  });
   return check_status(c);
 }
 

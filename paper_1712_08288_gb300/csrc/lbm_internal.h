@@ -140,12 +140,16 @@ cudaError_t launch_import_state(int lattice, int precision, const AuxArgs &a, co
 cudaError_t launch_loss(int lattice, int precision, const AuxArgs &a, const void *g,
                         const uint8_t *mask, const double *u_target, void *lam, double *J,
                         cudaStream_t st);
+// one step of the adjoint sweep: lambda(t) from lambda(t+1) and the pre-collision
+// state f (natural layout, compute type); per-link sums into link_acc (2 compute-type
+// values per link), dJ/ds into the per-block partial records
 cudaError_t launch_adjoint_step(int lattice, int precision, const SweepArgs<double> &a64,
-                                const SweepArgs<float> &a32, const AuxArgs &a, const double *link_q,
-                                const double *link_ephi, double *grad_q, double *grad_phi,
-                                double c0, double c1, double c2, double b, double rho0,
-                                const void *f, const void *lam_in, void *lam_out,
+                                const SweepArgs<float> &a32, const AuxArgs &a, const void *dcoef,
+                                void *link_acc, const void *f, const void *lam_in, void *lam_out,
                                 double *gs_part, cudaStream_t st);
+// tot[j] += link_acc[j], link_acc[j] = 0 for j < n
+cudaError_t launch_link_flush(int precision, void *link_acc, double *tot, long long n,
+                              cudaStream_t st);
 // per-block partial sums of dJ/ds (Q doubles per block), reduced by launch_adjoint_finish
 long long adjoint_partial_blocks(long long N);
 cudaError_t launch_adjoint_finish(int lattice, const double *gs_part, long long n_blocks,

@@ -171,3 +171,34 @@ def test_autograd_function():
     assert np.allclose(q.grad.numpy(), 3 * gq, rtol=0, atol=1e-15 + 1e-13 * np.abs(gq).max())
     assert np.allclose(s.grad.numpy(), 3 * gs, rtol=0, atol=1e-15 + 1e-13 * np.abs(gs).max())
     assert np.allclose(uw.grad.numpy(), 3 * gp, rtol=0, atol=1e-15 + 1e-13 * np.abs(gp).max())
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-6), ("f32", 2e-3)])
+def test_adjoint_ds_vs_central_differences_large_grid(prec, tol):
+    """An 80^3 periodic box (512,000 nodes, many thread blocks per SM) with a sphere:
+    dJ/ds_nu summed over the viscous rows against central differences of the FP64
+    forward run with h = 1e-4.  Catches per-block or per-thread accumulation that
+    drops nodes on large grids."""
+    w = W.sphere_3d(80, 12.5, (40.3, 39.8, 40.6), s_nu=1.0, force=(1e-5, 0.0, 0.0))
+    N = 80 ** 3
+    x = np.arange(N) % 80
+    mask = (x >= 60) & (x < 66)
+    rng = np.random.default_rng(21)
+    ut = 1e-4 * rng.standard_normal((N, 3))
+    steps = 30
+    viscous = [9, 11, 13, 14, 15]
+    sim = gpu_sim(w, prec)
+    sim.init_equilibrium()
+    J, gs, gq, gp = sim.adjoint(steps, mask, ut)
+
+    def J_of(sv):
+        s2 = gpu_sim(w, "f64")
+        S = w["S"].copy()
+        S[viscous] = sv
+        s2.set_relaxation(S)
+        s2.init_equilibrium()
+        return s2.adjoint(steps, mask, ut)[0]
+
+    h = 1e-4
+    fd = (J_of(1.0 + h) - J_of(1.0 - h)) / (2 * h)
+    assert abs(gs[viscous].sum() - fd) <= tol * abs(fd)
