@@ -272,6 +272,11 @@ def run_gpu(args):
     if args.ensemble_steps > 0 and rank == 0:
         ens = run_ensemble(args, torch, stream)
 
+    # ---- grid refinement of the 2D curved-wall problem (order of convergence) ---
+    ref = None
+    if args.refine_max > 0 and rank == 0:
+        ref = run_refinement(args, torch, stream)
+
     # ---- adjoint: gradients through the whole run, sqrt(N) checkpointing --------
     adj = None
     if args.adjoint_steps > 0 and rank == 0:
@@ -303,6 +308,7 @@ def run_gpu(args):
                      "note": "FP64 storage and arithmetic, same workload"},
             "accuracy": acc,
             "ensemble": ens,
+            "refinement": ref,
             "adjoint": adj,
             "e2e": e2e,
             "gpu_launches": args.steps,
@@ -373,6 +379,60 @@ def run_ensemble(args, torch, stream):
             "alg_GBs": round(2 * 9 * 4 * nf * K / (ms_batch * 1e-3) / 1e9, 1),
             "tuned": {"order": B.Batch.ORDERS[order], "blocks_per_sm": blocks, "tiles": q["tiles"]},
             "workload": "D2Q9 circular Couette ensemble, seed 0, n ~ U{48..768}, FP32 deviations"}
+
+
+def run_refinement(args, torch, stream):
+    """Grid refinement of the circular Couette problem (D2Q9, curved walls, 64^2
+    configuration scaled by n/64 with diffusive scaling): each n runs in FP64 from
+    the analytic-equilibrium start until the relative change of u over 200 steps is
+    below 1e-10, then FP32 deviation storage runs the same number of steps; E_r
+    against the analytic profile and the least-squares order of both.  Throughput
+    at n = 2048 is timed separately (a fixed number of steps, not to steady state)."""
+    from paper_1712_08288_gb300 import workloads as W
+    sizes = [n for n in (32, 64, 128, 256, 512, 1024, 2048) if n <= args.refine_max]
+    chunk, tol = 200, 1e-10
+    out = {"sizes": sizes, "steady_tol": tol, "chunk": chunk, "f64": {}, "f32": {}}
+    t_start = time.perf_counter()
+    for n in sizes:
+        w = W.couette_config(n)
+        ue = np.nan_to_num(w["u_exact"])
+        sim = build_sim(w, "f64", torch, stream)
+        sim.init_equilibrium(None, ue)
+        sim.error_norms(ue, check=False)
+        steps, res = 0, 1.0
+        while res >= tol and steps < args.refine_max_steps:
+            sim.step(chunk)
+            steps += chunk
+            res = sim.error_norms(ue, check=False)["residual"]
+        e64 = sim.error_norms(ue, check=False)["l2_rel"]
+        del sim
+        s32 = build_sim(w, "f32", torch, stream)
+        s32.init_equilibrium(None, ue)
+        s32.step(steps)
+        e32 = s32.error_norms(ue, check=False)["l2_rel"]
+        del s32
+        out["f64"][str(n)] = {"E_r": e64, "steps": steps, "residual": res}
+        out["f32"][str(n)] = {"E_r": e32, "steps": steps}
+
+    def order(prec):
+        e = [out[prec][str(n)]["E_r"] for n in sizes]
+        return float(-np.polyfit(np.log(sizes), np.log(e), 1)[0]) if len(sizes) > 1 else None
+    out["order_f64"] = order("f64")
+    out["order_f32"] = order("f32")
+    out["seconds"] = round(time.perf_counter() - t_start, 1)
+    if args.refine_mlups_n > 0:
+        w = W.couette_config(args.refine_mlups_n)
+        nf = int((~w["solid"]).sum())
+        ue = np.nan_to_num(w["u_exact"])
+        out["throughput_n"] = args.refine_mlups_n
+        for prec, k in (("f32", 2000), ("f64", 500)):
+            sim = build_sim(w, prec, torch, stream)
+            sim.init_equilibrium(None, ue)
+            total, _ = time_steps(sim, torch, stream, k, 20, per_launch=False)
+            out[prec + "_mlups_at_n"] = round(nf * k / (total * 1e-3) / 1e6, 1)
+            del sim
+    out["workload"] = "D2Q9 circular Couette, 64^2 configuration scaled to n (diffusive scaling)"
+    return out
 
 
 def run_adjoint(args, torch, stream):
@@ -513,6 +573,9 @@ def main():
     ap.add_argument("--accuracy-steps", type=int, default=20000)
     ap.add_argument("--adjoint-L", type=int, default=128)
     ap.add_argument("--adjoint-steps", type=int, default=2000)
+    ap.add_argument("--refine-max", type=int, default=512)
+    ap.add_argument("--refine-max-steps", type=int, default=600000)
+    ap.add_argument("--refine-mlups-n", type=int, default=2048)
     ap.add_argument("--ensemble-count", type=int, default=96)
     ap.add_argument("--ensemble-steps", type=int, default=400)
     ap.add_argument("--cpu-L", type=int, default=48)
