@@ -482,16 +482,21 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
     }
     if (solid) continue;
 
-    // lanes on the periodic x-edges: the row windows cannot follow the wrap
+    // lanes on the periodic x-edges: the row windows cannot follow the wrap.  A step
+    // across x = 0 lands in column nx-1 of the row shifted by (+sy, +sz), across
+    // x = nx-1 in column 0 of the row shifted by (-sy, -sz).
     const bool xlo = ODD && x == 0, xhi = ODD && x == nxm1;
+    const int xw = xlo ? nxm1 : 0;
+    const int ysh = SKEW ? (xlo ? y + A.sy : y - A.sy) : y;
+    const int zsh = SKEW ? (xlo ? z + A.sz : z - A.sz) : z;
     if (ODD && (xlo || xhi)) {
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         const int ex = L::ex(i);
         if ((ex > 0 && xlo) || (ex < 0 && xhi)) {
-          const long long src = wrap_index(x, y, z, -ex, -L::ey(i), -L::ez(i), A.nx, A.ny, A.nz,
-                                           A.sy, A.sz);
-          g[i] = Storage<T>::load(pop + (I)L::opp(i) * S + (I)src);
+          const int yy = wrap1(ysh - L::ey(i), A.ny);
+          const int zz = L::D == 3 ? wrap1(zsh - L::ez(i), A.nz) : 0;
+          g[i] = Storage<T>::load(pop + (I)L::opp(i) * S + (I)xw + (I)A.nx * ((I)yy + (I)A.ny * zz));
         }
       }
     }
@@ -534,9 +539,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
           for (int i = 0; i < Q; ++i) {
             const int ex = L::ex(i);
             if ((ex > 0 && xhi) || (ex < 0 && xlo)) {
-              const long long dn = wrap_index(x, y, z, ex, L::ey(i), L::ez(i), A.nx, A.ny, A.nz,
-                                              A.sy, A.sz);
-              Storage<T>::store(pop + (I)i * S + (I)dn, gp[i]);
+              const int yy = wrap1(ysh + L::ey(i), A.ny);
+              const int zz = L::D == 3 ? wrap1(zsh + L::ez(i), A.nz) : 0;
+              Storage<T>::store(pop + (I)i * S + (I)xw + (I)A.nx * ((I)yy + (I)A.ny * zz), gp[i]);
             }
           }
         }
