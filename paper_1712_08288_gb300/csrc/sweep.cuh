@@ -324,7 +324,7 @@ __device__ __forceinline__ const char *align16(const E *p, int &off_elems) {
 // window rounded up to 16 bytes; off[] records where each first element landed.
 // The offsets are stored before lane 0's arrive (release), so a lane that has
 // waited on the barrier sees them.  All lanes call.
-template <class L, class T, bool ODD, class I>
+template <class L, class T, bool ODD, bool ALIGNED, class I>
 __device__ __forceinline__ void issue_tile(const SweepArgs<typename Storage<T>::C> &a,
                                            const TileDesc &td, unsigned char *stage, int *off,
                                            uint64_t *bar) {
@@ -332,8 +332,8 @@ __device__ __forceinline__ void issue_tile(const SweepArgs<typename Storage<T>::
   constexpr int W = StageShape<T>::kWidth;
   const int lane = threadIdx.x & 31;
   const int ty = td.yz & 0xffff, tz = td.yz >> 16;
-  const char *src = nullptr;
-  void *dst = nullptr;
+  const char *src = nullptr, *src2 = nullptr;
+  void *dst = nullptr, *dst2 = nullptr;
   uint32_t bytes = 0;
   if (lane < L::Q) {
     const int i = lane;
@@ -344,12 +344,43 @@ __device__ __forceinline__ void issue_tile(const SweepArgs<typename Storage<T>::
       zz = (L::D == 3) ? wrap1(tz - DirBits<L>::ez(i), a.nz) : 0;
       xs = td.x0 - DirBits<L>::ex(i);
     }
+    const T *pop = static_cast<const T *>(a.pop);
     const I elem = (I)slot * (I)a.S + (I)a.nx * ((I)yy + (I)a.ny * zz) + xs;
     int o;
-    src = align16(static_cast<const T *>(a.pop) + elem, o);
+    src = align16(pop + elem, o);
     off[i] = o;
     bytes = ((uint32_t)((o + kTileW) * (int)sizeof(T)) + 15u) & ~15u;
     dst = stage + (size_t)i * W * sizeof(T);
+    if constexpr (ODD && ALIGNED) {
+      // Windows that cross the periodic x-wrap (rows start on 16-byte boundaries):
+      // the element read across x = 0 (column nx-1 of the row shifted by (+sy, +sz))
+      // or across x = nx-1 (column 0 of the row shifted by (-sy, -sz)) comes from a
+      // second 16-byte copy placed where the window expects it, and the main copy
+      // stops at the row's end.
+      constexpr int E16 = 16 / (int)sizeof(T);
+      const int ex = DirBits<L>::ex(i);
+      const bool lo = ex > 0 && td.x0 == 0;
+      const bool hi = ex < 0 && td.x0 + kTileW > a.nx - 1;
+      if (lo || hi) {
+        const int sy = lo ? a.sy : -a.sy, sz = lo ? a.sz : -a.sz;
+        const int yw = wrap1(yy + sy, a.ny);
+        const int zw = (L::D == 3) ? wrap1(zz + sz, a.nz) : 0;
+        const I rw = (I)slot * (I)a.S + (I)a.nx * ((I)yw + (I)a.ny * zw);
+        if (lo) {
+          // main copy: [0, kTileW) behind a 16-byte gap; chunk [nx-E16, nx) in the gap
+          src = reinterpret_cast<const char *>(pop + elem + 1);
+          dst = stage + ((size_t)i * W + E16) * sizeof(T);
+          bytes = kTileW * sizeof(T);
+          src2 = reinterpret_cast<const char *>(pop + rw + (a.nx - E16));
+          dst2 = stage + (size_t)i * W * sizeof(T);
+        } else {
+          // main copy: [x0, nx); chunk [0, E16) of the wrapped row right after it
+          bytes = (uint32_t)((a.nx - td.x0) * (int)sizeof(T));
+          src2 = reinterpret_cast<const char *>(pop + rw);
+          dst2 = stage + ((size_t)i * W + (a.nx - td.x0)) * sizeof(T);
+        }
+      }
+    }
   } else if (lane == L::Q) {
     const int nrec = __popcll(td.bnd);
     int o;
@@ -358,11 +389,12 @@ __device__ __forceinline__ void issue_tile(const SweepArgs<typename Storage<T>::
     bytes = nrec > 0 ? (((uint32_t)((o + nrec) * (int)sizeof(uint32_t)) + 15u) & ~15u) : 0u;
     dst = stage + SL::kRec;
   }
-  const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
+  const uint32_t total = __reduce_add_sync(0xffffffffu, bytes + (src2 ? 16u : 0u));
   __syncwarp();
   if (lane == 0) mbar_arrive_expect_tx(bar, total);
   __syncwarp();
   if (bytes) bulk_copy_g2s(dst, src, bytes, bar);
+  if (src2) bulk_copy_g2s(dst2, src2, 16u, bar);
 }
 
 // resident blocks per SM the register budget is sized for
@@ -426,7 +458,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
   for (int s = 0; s < NS; ++s) {
     const int tile = gw + s * nw;
     if (tile < n_tiles)
-      issue_tile<L, T, ODD, I>(args_for<BATCH>(a, inst, tile_inst, tile), tiles[tile],
+      issue_tile<L, T, ODD, ALIGNED, I>(args_for<BATCH>(a, inst, tile_inst, tile), tiles[tile],
                                wsm + s * SL::kStage, offs + s * NO, &bars[s]);
   }
 
@@ -477,7 +509,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
       __syncwarp();   // stage s consumed: refill it with the tile NS rounds ahead
       const int nt = tile + NS * nw;
       if (nt < n_tiles)
-        issue_tile<L, T, ODD, I>(args_for<BATCH>(a, inst, tile_inst, nt), tiles[nt],
+        issue_tile<L, T, ODD, ALIGNED, I>(args_for<BATCH>(a, inst, tile_inst, nt), tiles[nt],
                                  wsm + s * SL::kStage, offs + s * NO, &bars[s]);
     }
     if (solid) continue;
@@ -489,7 +521,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
     const int xw = xlo ? nxm1 : 0;
     const int ysh = SKEW ? (xlo ? y + A.sy : y - A.sy) : y;
     const int zsh = SKEW ? (xlo ? z + A.sz : z - A.sz) : z;
-    if (ODD && (xlo || xhi)) {
+    if (ODD && !ALIGNED && (xlo || xhi)) {      // aligned rows: staged with the windows
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         const int ex = L::ex(i);
