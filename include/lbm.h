@@ -31,6 +31,10 @@
  *             (0,-1,-1),(0,1,-1),(0,-1,1); moments rho, e, eps, j_x, q_x, j_y,
  *             q_y, j_z, q_z, 3p_xx, 3pi_xx, p_ww, pi_ww, p_xy, p_yz, p_xz, m_x,
  *             m_y, m_z.
+ *   LBM_D3Q15 directions 0..14 in the paper's Appendix order: rest; +x,-x,+y,-y,
+ *             +z,-z; (1,1,1),(-1,1,1),(1,-1,1),(-1,-1,1),(1,1,-1),(-1,1,-1),
+ *             (1,-1,-1),(-1,-1,-1); moments (the Appendix matrix): rho, e, eps,
+ *             j_x, q_x, j_y, q_y, j_z, q_z, 3p_xx, p_ww, p_xy, p_yz, p_xz, m_xyz.
  *
  * Grid: nx*ny*nz nodes (nz = 1 for D2Q9), node index n = x + nx*(y + ny*z).
  *   Every axis is periodic; the x-wrap may be skewed (lbm_set_skew).  Walls that
@@ -61,7 +65,7 @@ extern "C" {
 
 typedef struct lbm_ctx lbm_ctx;
 
-enum lbm_lattice { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
+enum lbm_lattice { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q15 = 2 };
 
 /* Storage precision of the populations.  F64 stores and computes in double.
  * The _DEV variants store deviations g_i = f_i - w_i rho0 (the scheme is exact in
@@ -81,7 +85,7 @@ enum lbm_status {
 };
 
 /* Create a context on the current CUDA device.
- *   lattice   LBM_D2Q9 or LBM_D3Q19; nz must be 1 for D2Q9.
+ *   lattice   LBM_D2Q9, LBM_D3Q19 or LBM_D3Q15; nz must be 1 for D2Q9.
  *   nx,ny,nz  grid size, each >= 1 (>= 3 along any axis a fluid link crosses).
  *   s         Q relaxation rates in the moment order above (diagonal of S,
  *             Appendix); the rates of rho and j have no effect (conserved).

@@ -14,10 +14,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblbm.so")
 
-LBM_D2Q9, LBM_D3Q19 = 0, 1
+LBM_D2Q9, LBM_D3Q19, LBM_D3Q15 = 0, 1, 2
 LBM_F64, LBM_F32_DEV, LBM_BF16_DEV, LBM_F16_DEV = 0, 1, 2, 3
 PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32_DEV, "bf16": LBM_BF16_DEV, "f16": LBM_F16_DEV}
-LATTICES = {"D2Q9": LBM_D2Q9, "D3Q19": LBM_D3Q19}
+LATTICES = {"D2Q9": LBM_D2Q9, "D3Q19": LBM_D3Q19, "D3Q15": LBM_D3Q15}
 STATUS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA",
           -4: "LBM_ENONCONVEX", -5: "LBM_EDIVERGED", -6: "LBM_ETIMEOUT", -7: "LBM_ESTATE"}
 
@@ -109,7 +109,7 @@ class Lbm:
         self.shape = tuple(int(v) for v in shape)
         self.precision = precision
         self.rho0 = float(rho0)
-        self.Q = 9 if lattice == "D2Q9" else 19
+        self.Q = {"D2Q9": 9, "D3Q19": 19, "D3Q15": 15}[lattice]
         self.D = 2 if lattice == "D2Q9" else 3
         self.N = self.shape[0] * self.shape[1] * self.shape[2]
         s = np.ascontiguousarray(s, dtype=np.float64)

@@ -116,7 +116,8 @@ __host__ __device__ constexpr int nc_slot(int k) {
     if (!L::conserved(r)) ++s;
   return s;
 }
-static_assert(nc_slot<D3Q19>(19) <= 16 && nc_slot<D2Q9>(9) <= 16, "at most 16 relaxed rows");
+static_assert(nc_slot<D3Q19>(19) <= 16 && nc_slot<D3Q15>(15) <= 16 && nc_slot<D2Q9>(9) <= 16,
+              "at most 16 relaxed rows");
 
 // Transposing warp reduction of 16 values per lane: at each of the offsets 16, 8,
 // 4, 2 a lane keeps the half of its values that its lane bit selects and adds the
@@ -164,6 +165,20 @@ __device__ __forceinline__ void meq_adjoint(D3Q19, const C (&smu)[19], C jx, C j
   out[1] = (a + px) * jx - c23 * smu[4] + (smu[13] * jy + smu[15] * jz) * ir0;
   out[2] = (a + pyz + w) * jy - c23 * smu[6] + (smu[13] * jx + smu[14] * jz) * ir0;
   out[3] = (a + pyz - w) * jz - c23 * smu[8] + (smu[14] * jy + smu[15] * jx) * ir0;
+}
+
+template <class C>
+__device__ __forceinline__ void meq_adjoint(D3Q15, const C (&smu)[15], C jx, C jy, C jz, C ir0,
+                                            C (&out)[4]) {
+  out[0] = -smu[1] + smu[2];
+  const C a = (C(2) * smu[1] - C(10) * smu[2]) * ir0;    // e, eps: j^2, -5 j^2
+  const C px = C(4) * smu[9] * ir0;                      // 3p_xx along j_x
+  const C pyz = C(-2) * smu[9] * ir0;                    // 3p_xx along j_y, j_z
+  const C w = C(2) * smu[10] * ir0;                      // p_ww along j_y (-w along j_z)
+  const C c73 = C(7.0 / 3.0);
+  out[1] = (a + px) * jx - c73 * smu[4] + (smu[11] * jy + smu[13] * jz) * ir0;
+  out[2] = (a + pyz + w) * jy - c73 * smu[6] + (smu[11] * jx + smu[12] * jz) * ir0;
+  out[3] = (a + pyz - w) * jz - c73 * smu[8] + (smu[12] * jy + smu[13] * jx) * ir0;
 }
 
 // all moments of v in the pair form: m_k = sum_i M(k,i) v_i
@@ -451,6 +466,7 @@ long long adjoint_partial_blocks(long long N) { return (N + kAdjThreads - 1) / k
 cudaError_t launch_adjoint_finish(int lattice, const double *gs_part, long long n_blocks,
                                   double *grad_s, cudaStream_t st) {
   if (lattice == 0) gs_finish_kernel<9><<<9, 256, 0, st>>>(gs_part, n_blocks, grad_s);
+  else if (lattice == 2) gs_finish_kernel<15><<<15, 256, 0, st>>>(gs_part, n_blocks, grad_s);
   else gs_finish_kernel<19><<<19, 256, 0, st>>>(gs_part, n_blocks, grad_s);
   return cudaGetLastError();
 }

@@ -103,6 +103,7 @@ __host__ inline cudaError_t with_lattice(int lattice, F &&f) {
   switch (lattice) {
     case 0: return f(D2Q9{});
     case 1: return f(D3Q19{});
+    case 2: return f(D3Q15{});
     default: return cudaErrorInvalidValue;
   }
 }

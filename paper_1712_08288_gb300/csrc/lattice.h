@@ -124,6 +124,63 @@ struct D3Q19 {
   static constexpr int kNormJ = 10;
 };
 
+// D3Q15 of the paper's Appendix: velocities in the printed order (rest; +x,-x,+y,-y,
+// +z,-z; then the eight corners (1,1,1), (-1,1,1), (1,-1,1), (-1,-1,1), (1,1,-1),
+// (-1,1,-1), (1,-1,-1), (-1,-1,-1)), weights 2/9, 1/9, 1/72, and the printed M,
+// whose rows are the polynomials 1, |e|^2-2, (15|e|^4-55|e|^2+32)/2, e_x,
+// (5|e|^2-13)e_x/2, e_y, (5|e|^2-13)e_y/2, e_z, (5|e|^2-13)e_z/2, 3e_x^2-|e|^2,
+// e_y^2-e_z^2, e_x e_y, e_y e_z, e_x e_z, e_x e_y e_z.
+struct D3Q15 {
+  static constexpr int Q = 15;
+  static constexpr int D = 3;
+  static constexpr int kLattice = 2;
+  LBM_HD static constexpr int ex(int i) {
+    constexpr int t[15] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1};
+    return t[i];
+  }
+  LBM_HD static constexpr int ey(int i) {
+    constexpr int t[15] = {0, 0, 0, 1, -1, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1};
+    return t[i];
+  }
+  LBM_HD static constexpr int ez(int i) {
+    constexpr int t[15] = {0, 0, 0, 0, 0, 1, -1, 1, 1, 1, 1, -1, -1, -1, -1};
+    return t[i];
+  }
+  // faces pair as (1,2), (3,4), (5,6); corner i pairs with 21 - i
+  LBM_HD static constexpr int opp(int i) {
+    return i == 0 ? 0 : (i < 7 ? ((i & 1) ? i + 1 : i - 1) : 21 - i);
+  }
+  LBM_HD static constexpr int opp_rt(int i) { return opp(i); }
+  LBM_HD static constexpr double w(int i) { return i == 0 ? 2.0 / 9.0 : (i < 7 ? 1.0 / 9.0 : 1.0 / 72.0); }
+  LBM_HD static constexpr int M(int k, int i) {
+    const int x = ex(i), y = ey(i), z = ez(i), r2 = x * x + y * y + z * z;
+    switch (k) {
+      case 0: return 1;
+      case 1: return r2 - 2;
+      case 2: return (15 * r2 * r2 - 55 * r2 + 32) / 2;
+      case 3: return x;
+      case 4: return (5 * r2 - 13) * x / 2;
+      case 5: return y;
+      case 6: return (5 * r2 - 13) * y / 2;
+      case 7: return z;
+      case 8: return (5 * r2 - 13) * z / 2;
+      case 9: return 3 * x * x - r2;
+      case 10: return y * y - z * z;
+      case 11: return x * y;
+      case 12: return y * z;
+      case 13: return x * z;
+      default: return x * y * z;
+    }
+  }
+  LBM_HD static constexpr bool conserved(int k) { return k == 0 || k == 3 || k == 5 || k == 7; }
+  static constexpr int NP = 7;
+  LBM_HD static constexpr int pair_first(int p) {
+    constexpr int t[7] = {1, 3, 5, 7, 8, 9, 10};
+    return t[p];
+  }
+  static constexpr int kNormJ = 10;
+};
+
 // Runtime (non-constant index) access to the velocity components and opposites,
 // from bit masks built at compile time, so that no table lands in local memory.
 template <class L>
@@ -200,5 +257,14 @@ static_assert(lattice_is_consistent<D2Q9>(), "D2Q9 tables");
 static_assert(lattice_is_consistent<D3Q19>(), "D3Q19 tables");
 static_assert(row_norm2<D2Q9>(1) == 36 && row_norm2<D2Q9>(3) == D2Q9::kNormJ, "D2Q9 norms");
 static_assert(row_norm2<D3Q19>(1) == 2394 && row_norm2<D3Q19>(3) == D3Q19::kNormJ, "D3Q19 norms");
+static_assert(lattice_is_consistent<D3Q15>(), "D3Q15 tables");
+static_assert(row_norm2<D3Q15>(1) == 18 && row_norm2<D3Q15>(2) == 360 && row_norm2<D3Q15>(3) == D3Q15::kNormJ &&
+                  row_norm2<D3Q15>(4) == 40 && row_norm2<D3Q15>(14) == 8,
+              "D3Q15 norms");
+// the printed table's entries
+static_assert(D3Q15::M(2, 0) == 16 && D3Q15::M(2, 1) == -4 && D3Q15::M(2, 7) == 1 &&
+                  D3Q15::M(4, 1) == -4 && D3Q15::M(4, 2) == 4 && D3Q15::M(4, 7) == 1 &&
+                  D3Q15::M(11, 8) == -1 && D3Q15::M(14, 12) == 1 && D3Q15::M(14, 14) == -1,
+              "D3Q15 M");
 
 }  // namespace lbm

@@ -22,17 +22,24 @@ cudaError_t launch_sweep_d2q9(int, bool, const SweepArgs<double> &, const SweepA
                               const TileDesc *, int, int, cudaStream_t);
 cudaError_t launch_sweep_d3q19(int, bool, const SweepArgs<double> &, const SweepArgs<float> &,
                                const TileDesc *, int, int, cudaStream_t);
+cudaError_t launch_sweep_d3q15(int, bool, const SweepArgs<double> &, const SweepArgs<float> &,
+                               const TileDesc *, int, int, cudaStream_t);
 int error_norms_noalloc(int device, int lattice, int precision, const AuxArgs &a, bool odd,
                         const double *u_ref, double *out, cudaStream_t st, const char **why);
 cudaError_t launch_sweep_batch_d2q9(int, bool, const void *, const TileDesc *, const int *, int,
                                    bool, int, cudaStream_t, bool);
 cudaError_t launch_sweep_batch_d3q19(int, bool, const void *, const TileDesc *, const int *, int,
                                     bool, int, cudaStream_t, bool);
+cudaError_t launch_sweep_batch_d3q15(int, bool, const void *, const TileDesc *, const int *, int,
+                                    bool, int, cudaStream_t, bool);
 cudaError_t launch_sweep(int lattice, int precision, bool odd, const SweepArgs<double> &a64,
                          const SweepArgs<float> &a32, const TileDesc *tiles, int n_tiles, int bx,
                          cudaStream_t st) {
-  return lattice == LBM_D2Q9 ? launch_sweep_d2q9(precision, odd, a64, a32, tiles, n_tiles, bx, st)
-                             : launch_sweep_d3q19(precision, odd, a64, a32, tiles, n_tiles, bx, st);
+  switch (lattice) {
+    case LBM_D2Q9: return launch_sweep_d2q9(precision, odd, a64, a32, tiles, n_tiles, bx, st);
+    case LBM_D3Q15: return launch_sweep_d3q15(precision, odd, a64, a32, tiles, n_tiles, bx, st);
+    default: return launch_sweep_d3q19(precision, odd, a64, a32, tiles, n_tiles, bx, st);
+  }
 }
 }  // namespace lbm
 
@@ -120,7 +127,7 @@ static size_t pop_alloc_bytes(const lbm_ctx *c) {
 
 template <class F>
 static auto with_lat(int lattice, F &&f) {
-  return lattice == LBM_D2Q9 ? f(D2Q9{}) : f(D3Q19{});
+  return lattice == LBM_D2Q9 ? f(D2Q9{}) : (lattice == LBM_D3Q15 ? f(D3Q15{}) : f(D3Q19{}));
 }
 
 static long long wrap_host(const lbm_ctx *c, int x, int y, int z, int dx, int dy, int dz) {
@@ -306,7 +313,7 @@ int lbm_create(lbm_ctx **out, int lattice, int nx, int ny, int nz, const double 
                int precision, double rho0) {
   if (!out) return fail(nullptr, LBM_EINVAL, "lbm_create: out is NULL");
   *out = nullptr;
-  if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19)
+  if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19 && lattice != LBM_D3Q15)
     return fail(nullptr, LBM_EINVAL, "lbm_create: unknown lattice %d", lattice);
   if (precision < LBM_F64 || precision > LBM_F16_DEV)
     return fail(nullptr, LBM_EINVAL, "lbm_create: unknown precision %d", precision);
@@ -317,7 +324,7 @@ int lbm_create(lbm_ctx **out, int lattice, int nx, int ny, int nz, const double 
   if (!s) return fail(nullptr, LBM_EINVAL, "lbm_create: s is NULL");
   if (!(rho0 > 0) || !std::isfinite(rho0))
     return fail(nullptr, LBM_EINVAL, "lbm_create: rho0 must be > 0");
-  const int Q = lattice == LBM_D2Q9 ? 9 : 19;
+  const int Q = lattice == LBM_D2Q9 ? 9 : (lattice == LBM_D3Q15 ? 15 : 19);
   for (int k = 0; k < Q; ++k)
     if (!std::isfinite(s[k]) || s[k] < 0 || s[k] > 2)
       return fail(nullptr, LBM_EINVAL, "lbm_create: s[%d] = %g outside [0, 2]", k, s[k]);
@@ -1077,11 +1084,17 @@ static int batch_refresh_if_needed(lbm_batch *b) {
 }
 
 static cudaError_t batch_launch(lbm_batch *b, bool odd, bool prepare_only) {
-  return b->lattice == LBM_D2Q9
-             ? launch_sweep_batch_d2q9(b->precision, odd, b->inst, b->tiles, b->tile_inst, b->n_tiles,
-                                       b->big, b->blocks_per_sm, b->stream, prepare_only)
-             : launch_sweep_batch_d3q19(b->precision, odd, b->inst, b->tiles, b->tile_inst,
-                                        b->n_tiles, b->big, b->blocks_per_sm, b->stream, prepare_only);
+  switch (b->lattice) {
+    case LBM_D2Q9:
+      return launch_sweep_batch_d2q9(b->precision, odd, b->inst, b->tiles, b->tile_inst, b->n_tiles,
+                                     b->big, b->blocks_per_sm, b->stream, prepare_only);
+    case LBM_D3Q15:
+      return launch_sweep_batch_d3q15(b->precision, odd, b->inst, b->tiles, b->tile_inst, b->n_tiles,
+                                      b->big, b->blocks_per_sm, b->stream, prepare_only);
+    default:
+      return launch_sweep_batch_d3q19(b->precision, odd, b->inst, b->tiles, b->tile_inst, b->n_tiles,
+                                      b->big, b->blocks_per_sm, b->stream, prepare_only);
+  }
 }
 
 static int batch_check_parity(lbm_batch *b, bool *odd) {

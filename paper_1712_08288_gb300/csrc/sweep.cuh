@@ -32,8 +32,9 @@ namespace lbm {
 
 // Equilibrium moments m^eq_k in deviation form (rho replaced by rho - rho0) for
 // the incompressible equilibrium of Eq. 42, j = rho0 u.  These are the closed forms
-// of M f^eq for the two moment bases (Lallemand & Luo 2000 for D2Q9; d'Humieres
-// et al. 2002 for D3Q19 with w_eps = 3, w_epsj = -11/2, w_xx = -1/2).
+// of M f^eq for the moment bases (Lallemand & Luo 2000 for D2Q9; d'Humieres et
+// al. 2002 for D3Q19 with w_eps = 3, w_epsj = -11/2, w_xx = -1/2; the Appendix's
+// D3Q15 basis below).
 template <class C>
 __device__ __forceinline__ C meq(D2Q9, int k, C drho, C jx, C jy, C, C ir0) {
   switch (k) {
@@ -62,6 +63,26 @@ __device__ __forceinline__ C meq(D3Q19, int k, C drho, C jx, C jy, C jz, C ir0) 
     case 13: return jx * jy * ir0;
     case 14: return jy * jz * ir0;
     case 15: return jx * jz * ir0;
+    default: return C(0);
+  }
+}
+
+// D3Q15 (Appendix basis): e^eq = -rho + j^2/rho0, eps^eq = rho - 5 j^2/rho0,
+// q^eq = -7/3 j, second-order rows j_a j_b / rho0 combinations, m_xyz^eq = 0
+template <class C>
+__device__ __forceinline__ C meq(D3Q15, int k, C drho, C jx, C jy, C jz, C ir0) {
+  const C j2 = (jx * jx + jy * jy + jz * jz) * ir0;
+  switch (k) {
+    case 1: return -drho + j2;
+    case 2: return drho - C(5) * j2;
+    case 4: return C(-7.0 / 3.0) * jx;
+    case 6: return C(-7.0 / 3.0) * jy;
+    case 8: return C(-7.0 / 3.0) * jz;
+    case 9: return C(3) * jx * jx * ir0 - j2;
+    case 10: return (jy * jy - jz * jz) * ir0;
+    case 11: return jx * jy * ir0;
+    case 12: return jy * jz * ir0;
+    case 13: return jx * jz * ir0;
     default: return C(0);
   }
 }

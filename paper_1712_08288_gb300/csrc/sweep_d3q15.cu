@@ -1,0 +1,31 @@
+// sweep_d3q15.cu -- D3Q15 instantiations of the fused collide / stream / boundary sweep
+// (storage: FP64, FP32 deviations, BF16 deviations, FP16 deviations).
+#include "sweep.cuh"
+
+namespace lbm {
+
+cudaError_t launch_sweep_d3q15(int precision, bool odd, const SweepArgs<double> &a64,
+                           const SweepArgs<float> &a32, const TileDesc *tiles, int n_tiles,
+                           int bx, cudaStream_t st) {
+  switch (precision) {
+    case 0: return launch_sweep_t<D3Q15, double>(odd, a64, tiles, n_tiles, bx, st);
+    case 1: return launch_sweep_t<D3Q15, float>(odd, a32, tiles, n_tiles, bx, st);
+    case 2: return launch_sweep_t<D3Q15, __nv_bfloat16>(odd, a32, tiles, n_tiles, bx, st);
+    case 3: return launch_sweep_t<D3Q15, __half>(odd, a32, tiles, n_tiles, bx, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_sweep_batch_d3q15(int precision, bool odd, const void *inst, const TileDesc *tiles,
+                                 const int *tile_inst, int n_tiles, bool big, int blocks_per_sm,
+                                 cudaStream_t st, bool prepare_only) {
+  switch (precision) {
+    case 0: return launch_sweep_batch_t<D3Q15, double>(odd, static_cast<const SweepArgs<double> *>(inst), tiles, tile_inst, n_tiles, big, blocks_per_sm, st, prepare_only);
+    case 1: return launch_sweep_batch_t<D3Q15, float>(odd, static_cast<const SweepArgs<float> *>(inst), tiles, tile_inst, n_tiles, big, blocks_per_sm, st, prepare_only);
+    case 2: return launch_sweep_batch_t<D3Q15, __nv_bfloat16>(odd, static_cast<const SweepArgs<float> *>(inst), tiles, tile_inst, n_tiles, big, blocks_per_sm, st, prepare_only);
+    case 3: return launch_sweep_batch_t<D3Q15, __half>(odd, static_cast<const SweepArgs<float> *>(inst), tiles, tile_inst, n_tiles, big, blocks_per_sm, st, prepare_only);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace lbm

@@ -23,8 +23,9 @@ The direction tables below are the C-ABI's numbering (plain data).
 
 import numpy as np
 
-# C-ABI direction numbering.  D2Q9 follows the paper's Appendix order; D3Q19 is
-# rest, +x,-x,+y,-y,+z,-z, then the twelve edges, each followed by its opposite.
+# C-ABI direction numbering.  D2Q9 and D3Q15 follow the paper's Appendix order;
+# D3Q19 is rest, +x,-x,+y,-y,+z,-z, then the twelve edges, each followed by its
+# opposite.
 DIRECTIONS = {
     "D2Q9": np.array([(0, 0, 0), (1, 0, 0), (0, 1, 0), (-1, 0, 0), (0, -1, 0),
                       (1, 1, 0), (-1, 1, 0), (-1, -1, 0), (1, -1, 0)], dtype=np.int64),
@@ -34,6 +35,12 @@ DIRECTIONS = {
         (1, 1, 0), (-1, -1, 0), (1, -1, 0), (-1, 1, 0),
         (1, 0, 1), (-1, 0, -1), (1, 0, -1), (-1, 0, 1),
         (0, 1, 1), (0, -1, -1), (0, 1, -1), (0, -1, 1)], dtype=np.int64),
+    # D3Q15 in the paper's Appendix order: rest, faces, then the eight corners
+    "D3Q15": np.array([
+        (0, 0, 0),
+        (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1),
+        (1, 1, 1), (-1, 1, 1), (1, -1, 1), (-1, -1, 1),
+        (1, 1, -1), (-1, 1, -1), (1, -1, -1), (-1, -1, -1)], dtype=np.int64),
 }
 
 
@@ -47,12 +54,16 @@ def relaxation_rates(lattice, s_nu):
     D3Q19 (rows rho, e, eps, j_x, q_x, j_y, q_y, j_z, q_z, 3p_xx, 3pi_xx, p_ww,
     pi_ww, p_xy, p_yz, p_xz, m_x, m_y, m_z): the paper's D3Q15 choice mapped onto
     these rows; the fourth-order pi moments take 1.2, the third-order m moments 1.5.
+    D3Q15 (rows rho, e, eps, j_x, q_x, j_y, q_y, j_z, q_z, 3p_xx, p_ww, p_xy, p_yz,
+    p_xz, m_xyz): the vector the paper prints in Sec. 3.
     """
     if lattice == "D2Q9":
         s = [1, 1.8, 1.2, 1, 0.5, 1, 0.5, s_nu, s_nu]
     elif lattice == "D3Q19":
         s = [1, 1.8, 1.2, 1, 0.5, 1, 0.5, 1, 0.5,
              s_nu, 1.2, s_nu, 1.2, s_nu, s_nu, s_nu, 1.5, 1.5, 1.5]
+    elif lattice == "D3Q15":
+        s = [1, 1.8, 1.2, 1, 0.5, 1, 0.5, 1, 0.5, s_nu, s_nu, s_nu, s_nu, s_nu, 1.5]
     else:
         raise ValueError(lattice)
     return np.array(s, dtype=np.float64)
