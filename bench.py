@@ -231,6 +231,22 @@ def run_gpu(args):
     ach64 = 2 * Q * BYTES["f64"] * n_fluid / (l64 * 1e-3) / 1e9
     del sim
 
+    # ---- D3Q15 (the paper's own 3D lattice) on the same workload --------------
+    d15 = None
+    if args.d3q15_steps > 0:
+        w15 = W.tilted_pipe_3d(L, lattice="D3Q15")
+        nf15 = int((~w15["solid"]).sum())
+        d15 = {"workload": "the same pipe, D3Q15 (Appendix velocities, M and S)"}
+        for prec, k in (("f32", args.d3q15_steps), ("f64", max(10, args.d3q15_steps // 8))):
+            sim = build_sim(w15, prec, torch, stream)
+            sim.init_equilibrium(None, np.nan_to_num(w15["u_exact"]))
+            tot, ls = time_steps(sim, torch, stream, k, min(args.warmup, 10))
+            lm = float(np.mean(ls))
+            gbs = 2 * 15 * BYTES[prec] * nf15 / (lm * 1e-3) / 1e9
+            d15[prec] = {"mlups": round(nf15 * k / (tot * 1e-3) / 1e6, 1), "steps": k,
+                         "achieved_GBs": round(gbs, 1), "frac_of_hbm": round(gbs / hbm, 4)}
+            del sim
+
     # ---- e2e through the C-ABI with host buffers ------------------------------
     sim = build_sim(w, "f32", torch, stream)
     N = L ** 3
@@ -306,6 +322,7 @@ def run_gpu(args):
                      "launch_ms": l64, "achieved_GBs": round(ach64, 1),
                      "frac_of_hbm": round(ach64 / hbm, 4),
                      "note": "FP64 storage and arithmetic, same workload"},
+            "d3q15": d15,
             "accuracy": acc,
             "ensemble": ens,
             "refinement": ref,
@@ -573,6 +590,7 @@ def main():
     ap.add_argument("--accuracy-steps", type=int, default=20000)
     ap.add_argument("--adjoint-L", type=int, default=128)
     ap.add_argument("--adjoint-steps", type=int, default=2000)
+    ap.add_argument("--d3q15-steps", type=int, default=1000)
     ap.add_argument("--refine-max", type=int, default=512)
     ap.add_argument("--refine-max-steps", type=int, default=600000)
     ap.add_argument("--refine-mlups-n", type=int, default=2048)
