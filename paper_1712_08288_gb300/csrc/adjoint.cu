@@ -240,7 +240,21 @@ __global__ void __launch_bounds__(kAdjThreads, sizeof(C) == 4 ? LBM_ADJ_MINB_F32
     // advection transpose: lambda'_i(x) = lambda_i(x + e_i); solid entries of the
     // adjoint are kept at zero, so no class test is needed.  Neighbours follow the
     // periodic wrap, skewed along x by (sy, sz).
-    if constexpr (SMALL) {
+    const bool inside = x > 0 && x < a.nx - 1 && y > 0 && y < a.ny - 1 &&
+                        (L::D == 2 || (z > 0 && z < a.nz - 1));
+    if (inside) {
+      // away from the faces of the box: a constant offset per direction
+      const long long sx = a.nx, sxy = (long long)a.nx * a.ny;
+      const C *base = lam_in + n;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        long long o = (long long)i * N;
+        if (L::ex(i)) o += L::ex(i);
+        if (L::ey(i)) o += L::ey(i) > 0 ? sx : -sx;
+        if (L::ez(i)) o += L::ez(i) > 0 ? sxy : -sxy;
+        lp[i] = base[o];
+      }
+    } else if constexpr (SMALL) {
       const Neighbours<L, true> nb(x, y, z, a.nx, a.ny, a.nz, a.sy, a.sz);
 #pragma unroll
       for (int i = 0; i < Q; ++i) lp[i] = lam_in[(long long)i * N + nb(i)];
@@ -347,6 +361,76 @@ __global__ void __launch_bounds__(kAdjThreads, sizeof(C) == 4 ? LBM_ADJ_MINB_F32
   }
 }
 
+// One forward step in the natural layout, for recomputing a segment (push form):
+// every fluid node collides its pre-collision populations f(t) (fin) and sends
+// f'_i to slot i of x + e_i in fout, which then holds f(t+1); the populations that
+// arrive through a cut link come from the single-node scheme (Eqs. 2.10, 2.13)
+// into the node's own slot.  Same arithmetic as the fused sweep, so the states
+// agree with the forward run's; slots of solid nodes receive values nobody reads.
+// Reads and writes Q values per node, against the sweep-with-save's three.
+template <class L, class C, bool SMALL>
+__global__ void __launch_bounds__(kAdjThreads, sizeof(C) == 4 ? 6 : 3)
+    recompute_step_kernel(const SweepArgs<C> sa, AuxArgs a, const C *__restrict__ fin,
+                          C *__restrict__ fout) {
+  constexpr int Q = L::Q;
+  const long long N = a.N;
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  C g[Q], gp[Q];
+  const uint8_t cls = a.cls[n];
+  if (cls == kSolid) return;
+  int x, y, z;
+  {
+    const long long r = n / a.nx;
+    x = (int)(n - r * a.nx);
+    y = (int)(r % a.ny);
+    z = (int)(r / a.ny);
+  }
+#pragma unroll
+  for (int i = 0; i < Q; ++i) g[i] = fin[(long long)i * N + n];
+  C drho;
+  collide<L, C>(g, gp, sa, drho);
+  if (!(fabs(drho) < C(1e6))) atomicOr(sa.status, 1);
+  const bool inside = x > 0 && x < a.nx - 1 && y > 0 && y < a.ny - 1 &&
+                      (L::D == 2 || (z > 0 && z < a.nz - 1));
+  if (inside) {
+    const long long sx = a.nx, sxy = (long long)a.nx * a.ny;
+    C *base = fout + n;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      long long o = (long long)i * N;
+      if (L::ex(i)) o += L::ex(i);
+      if (L::ey(i)) o += L::ey(i) > 0 ? sx : -sx;
+      if (L::ez(i)) o += L::ez(i) > 0 ? sxy : -sxy;
+      base[o] = gp[i];
+    }
+  } else if constexpr (SMALL) {
+    const Neighbours<L, true> nb(x, y, z, a.nx, a.ny, a.nz, a.sy, a.sz);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fout[(long long)i * N + nb(i)] = gp[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+      fout[(long long)i * N + wrap_index(x, y, z, L::ex(i), L::ey(i), L::ez(i), a.nx, a.ny, a.nz,
+                                         a.sy, a.sz)] = gp[i];
+  }
+  if (cls == kBoundary) {
+    const LinkCoef<C> *coef = static_cast<const LinkCoef<C> *>(sa.geo.coef);
+    const int bi = a.bidx[n];
+    const uint32_t mask = a.bmask[bi];
+    const int off = a.boff[bi];
+#pragma unroll
+    for (int dd = 1; dd < Q; ++dd) {
+      if (mask & (1u << dd)) {
+        const LinkCoef<C> c = coef[off + __popc(mask & ((1u << dd) - 1u))];
+        const int i = L::opp(dd);
+        fout[(long long)i * N + n] =
+            sa.one_minus_b * g[i] + c.a * g[dd] + c.bb * gp[i] + c.c * gp[dd] + c.w;
+      }
+    }
+  }
+}
+
 // add the per-link sums of one segment to the FP64 totals and clear them
 template <class C>
 __global__ void link_flush_kernel(C *acc, double *tot, long long n) {
@@ -438,6 +522,29 @@ cudaError_t launch_adjoint_step(int lattice, int precision, const SweepArgs<doub
       adjoint_step_kernel<L, C, decltype(sm)::value><<<blocks, kAdjThreads, 0, st>>>(
           sa, a, ag, static_cast<const C *>(f), static_cast<const C *>(lam_in),
           static_cast<C *>(lam_out), gs_part);
+    };
+    if (precision == 0) {
+      if (small) go(a64, std::true_type{});
+      else go(a64, std::false_type{});
+    } else {
+      if (small) go(a32, std::true_type{});
+      else go(a32, std::false_type{});
+    }
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_recompute_step(int lattice, int precision, const SweepArgs<double> &a64,
+                                  const SweepArgs<float> &a32, const AuxArgs &a, const void *fin,
+                                  void *fout, cudaStream_t st) {
+  const unsigned blocks = (unsigned)adjoint_partial_blocks(a.N);
+  const bool small = a.N < (1LL << 31);
+  return with_lattice(lattice, [&](auto lat) {
+    using L = decltype(lat);
+    auto go = [&](const auto &sa, auto sm) {
+      using C = std::remove_cv_t<std::remove_reference_t<decltype(sa.inv_rho0)>>;
+      recompute_step_kernel<L, C, decltype(sm)::value><<<blocks, kAdjThreads, 0, st>>>(
+          sa, a, static_cast<const C *>(fin), static_cast<C *>(fout));
     };
     if (precision == 0) {
       if (small) go(a64, std::true_type{});

@@ -806,7 +806,8 @@ int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *ma
                   cudaGetErrorString(e_));                                                  \
     }                                                                                       \
   } while (0)
-  ADJ_CUDA(cudaMalloc((void **)&ck, (raw_pop + raw_lnk) * nseg));
+  ADJ_CUDA(cudaMalloc((void **)&ck, (c->precision == LBM_F64 || c->precision == LBM_F32_DEV
+                                        ? state : raw_pop + raw_lnk) * nseg));
   ADJ_CUDA(cudaMalloc((void **)&seg, state * K));
   ADJ_CUDA(cudaMalloc((void **)&fin, raw_pop + raw_lnk));
   ADJ_CUDA(cudaMalloc((void **)&lam0, state));
@@ -856,35 +857,66 @@ int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *ma
     return e;
   };
   const long long t0 = c->t;
-  // forward pass with checkpoints every K steps
-  for (long long sgm = 0; sgm < nseg; ++sgm) {
-    ADJ_CUDA(save_raw(ck + (raw_pop + raw_lnk) * sgm));
-    tck[sgm] = c->t;
-    const int len = (int)std::min(K, T - sgm * K);
-    if ((rc = lbm_step(c, len)) != LBM_OK) { cleanup(); return rc; }
-  }
-  ADJ_CUDA(save_raw(fin));
-  // loss and lambda(T)
-  ADJ_CUDA(launch_export_state(c->lattice, c->precision, aux_args(c), (c->t & 1) != 0, seg, st));
-  ADJ_CUDA(launch_loss(c->lattice, c->precision, aux_args(c), seg, dmask, dut, lam0, dJ, st));
-  // backward pass: recompute each segment from its checkpoint, then step back
-  char *lin = lam0, *lout = lam1;
-  for (long long sgm = nseg - 1; sgm >= 0; --sgm) {
-    ADJ_CUDA(load_raw(ck + (raw_pop + raw_lnk) * sgm));
-    c->t = tck[sgm];
-    const int len = (int)std::min(K, T - sgm * K);
+  // steps of a segment that also write each step's pre-collision state
+  auto step_saving = [&](int len) -> int {
     for (int r = 0; r < len; ++r) {
-      // the recomputing sweep also writes the pre-collision state of step r
       if (c->precision == LBM_F64) c->a64.save = reinterpret_cast<double *>(seg + state * r);
       else c->a32.save = reinterpret_cast<float *>(seg + state * r);
-      rc = lbm_step(c, 1);
+      const int e = lbm_step(c, 1);
       c->a64.save = nullptr;
       c->a32.save = nullptr;
-      if (rc != LBM_OK) { cleanup(); return rc; }
+      if (e != LBM_OK) return e;
+    }
+    return LBM_OK;
+  };
+  // FP64 and FP32 storage (storage type = compute type) recompute segments with the
+  // push-form step in the natural layout, from natural-layout checkpoints: a step
+  // then reads and writes Q values per node instead of the sweep's three.  16-bit
+  // storage recomputes with the sweep itself, from raw checkpoints, so that its
+  // rounding matches the forward run.
+  const bool natural = c->precision == LBM_F64 || c->precision == LBM_F32_DEV;
+  const size_t ck_bytes = natural ? state : raw_pop + raw_lnk;
+  // forward pass with checkpoints every K steps; the last segment keeps its states
+  // as it goes, so the backward pass need not recompute it
+  for (long long sgm = 0; sgm < nseg; ++sgm) {
+    if (natural)
+      ADJ_CUDA(launch_export_state(c->lattice, c->precision, aux_args(c), (c->t & 1) != 0,
+                                   ck + ck_bytes * sgm, st));
+    else
+      ADJ_CUDA(save_raw(ck + ck_bytes * sgm));
+    tck[sgm] = c->t;
+    const int len = (int)std::min(K, T - sgm * K);
+    rc = sgm == nseg - 1 ? step_saving(len) : lbm_step(c, len);
+    if (rc != LBM_OK) { cleanup(); return rc; }
+  }
+  ADJ_CUDA(save_raw(fin));
+  // loss and lambda(T) (the final state goes through lam1, which the first adjoint
+  // step overwrites)
+  ADJ_CUDA(launch_export_state(c->lattice, c->precision, aux_args(c), (c->t & 1) != 0, lam1, st));
+  ADJ_CUDA(launch_loss(c->lattice, c->precision, aux_args(c), lam1, dmask, dut, lam0, dJ, st));
+  // backward pass: recompute each earlier segment from its checkpoint, then step back
+  char *lin = lam0, *lout = lam1;
+  for (long long sgm = nseg - 1; sgm >= 0; --sgm) {
+    const int len = (int)std::min(K, T - sgm * K);
+    const bool last = sgm == nseg - 1;
+    // state of step r of this segment: the natural checkpoint itself for r = 0
+    auto at = [&](int r) -> char * {
+      return (natural && !last && r == 0) ? ck + ck_bytes * sgm : seg + state * r;
+    };
+    if (!last) {
+      if (natural) {
+        for (int r = 0; r + 1 < len; ++r)
+          ADJ_CUDA(launch_recompute_step(c->lattice, c->precision, c->a64, c->a32, aux_args(c),
+                                         at(r), at(r + 1), st));
+      } else {
+        ADJ_CUDA(load_raw(ck + ck_bytes * sgm));
+        c->t = tck[sgm];
+        if ((rc = step_saving(len)) != LBM_OK) { cleanup(); return rc; }
+      }
     }
     for (int r = len - 1; r >= 0; --r) {
       ADJ_CUDA(launch_adjoint_step(c->lattice, c->precision, c->a64, c->a32, aux_args(c), dcoef,
-                                   acc, seg + state * r, lin, lout, gpart, st));
+                                   acc, at(r), lin, lout, gpart, st));
       std::swap(lin, lout);
     }
     ADJ_CUDA(launch_link_flush(c->precision, acc, dtot, 2 * nl, st));

@@ -147,6 +147,11 @@ cudaError_t launch_adjoint_step(int lattice, int precision, const SweepArgs<doub
                                 const SweepArgs<float> &a32, const AuxArgs &a, const void *dcoef,
                                 void *link_acc, const void *f, const void *lam_in, void *lam_out,
                                 double *gs_part, cudaStream_t st);
+// f(t+1) from f(t), both natural layout in the compute type (push form, same
+// arithmetic as the sweep); for recomputing adjoint segments of FP64 / FP32 storage
+cudaError_t launch_recompute_step(int lattice, int precision, const SweepArgs<double> &a64,
+                                  const SweepArgs<float> &a32, const AuxArgs &a, const void *fin,
+                                  void *fout, cudaStream_t st);
 // tot[j] += link_acc[j], link_acc[j] = 0 for j < n
 cudaError_t launch_link_flush(int precision, void *link_acc, double *tot, long long n,
                               cudaStream_t st);

@@ -539,19 +539,23 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
     // across x = 0 lands in column nx-1 of the row shifted by (+sy, +sz), across
     // x = nx-1 in column 0 of the row shifted by (-sy, -sz).
     const bool xlo = ODD && x == 0, xhi = ODD && x == nxm1;
-    const int xw = xlo ? nxm1 : 0;
-    const int ysh = SKEW ? (xlo ? y + A.sy : y - A.sy) : y;
-    const int zsh = SKEW ? (xlo ? z + A.sz : z - A.sz) : z;
-    if (ODD && !ALIGNED && (xlo || xhi)) {      // aligned rows: staged with the windows
+    // node index in the row (y + dy, z + dz) shifted across the wrap, column xc
+    auto across = [&](int xc, int dy, int dz) -> I {
+      const int yy = wrap1(y + dy, A.ny);
+      const int zz = L::D == 3 ? wrap1(z + dz, A.nz) : 0;
+      return (I)xc + (I)A.nx * ((I)yy + (I)A.ny * zz);
+    };
+    const int sy = SKEW ? A.sy : 0, sz = SKEW ? A.sz : 0;
+    if (ODD && !ALIGNED && xlo) {          // aligned rows: staged with the windows
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const int ex = L::ex(i);
-        if ((ex > 0 && xlo) || (ex < 0 && xhi)) {
-          const int yy = wrap1(ysh - L::ey(i), A.ny);
-          const int zz = L::D == 3 ? wrap1(zsh - L::ez(i), A.nz) : 0;
-          g[i] = Storage<T>::load(pop + (I)L::opp(i) * S + (I)xw + (I)A.nx * ((I)yy + (I)A.ny * zz));
-        }
-      }
+      for (int i = 0; i < Q; ++i)
+        if (L::ex(i) > 0)
+          g[i] = Storage<T>::load(pop + (I)L::opp(i) * S + across(nxm1, sy - L::ey(i), sz - L::ez(i)));
+    } else if (ODD && !ALIGNED && xhi) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+        if (L::ex(i) < 0)
+          g[i] = Storage<T>::load(pop + (I)L::opp(i) * S + across(0, -sy - L::ey(i), -sz - L::ez(i)));
     }
     if (ODD && bmask) {
       // populations that arrive through a cut link were left in the link buffer
@@ -587,16 +591,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
           if ((ex > 0 && xhi) || (ex < 0 && xlo)) continue;   // crosses the x-wrap
           Storage<T>::store(pn + (I)A.koff_odd[i], gp[i]);     // slot i of x + e_i
         }
-        if (xlo || xhi) {
+        if (xlo) {
 #pragma unroll
-          for (int i = 0; i < Q; ++i) {
-            const int ex = L::ex(i);
-            if ((ex > 0 && xhi) || (ex < 0 && xlo)) {
-              const int yy = wrap1(ysh + L::ey(i), A.ny);
-              const int zz = L::D == 3 ? wrap1(zsh + L::ez(i), A.nz) : 0;
-              Storage<T>::store(pop + (I)i * S + (I)xw + (I)A.nx * ((I)yy + (I)A.ny * zz), gp[i]);
-            }
-          }
+          for (int i = 0; i < Q; ++i)
+            if (L::ex(i) < 0)
+              Storage<T>::store(pop + (I)i * S + across(nxm1, sy + L::ey(i), sz + L::ez(i)), gp[i]);
+        } else if (xhi) {
+#pragma unroll
+          for (int i = 0; i < Q; ++i)
+            if (L::ex(i) > 0)
+              Storage<T>::store(pop + (I)i * S + across(0, -sy + L::ey(i), -sz + L::ez(i)), gp[i]);
         }
       } else {
         // rows of the tile touch a periodic edge in y or z: wrap every neighbour

@@ -202,3 +202,22 @@ def test_adjoint_ds_vs_central_differences_large_grid(prec, tol):
     h = 1e-4
     fd = (J_of(1.0 + h) - J_of(1.0 - h)) / (2 * h)
     assert abs(gs[viscous].sum() - fd) <= tol * abs(fd)
+
+
+def test_bf16_storage_adjoint_recomputes_with_the_sweep():
+    """16-bit storage recomputes segments with the sweep itself (raw checkpoints):
+    the gradients stay close to the FP64 adjoint's (BF16 rounds every step)."""
+    w = _case("pipe")
+    rho, u, mask, ut = _inputs(w, 11)
+    res = {}
+    for prec in ("f64", "bf16"):
+        g = gpu_sim(w, prec)
+        g.init_equilibrium(rho, u)
+        res[prec] = g.adjoint(20, mask, ut, checkpoint_every=6)
+    J64, gs64, gq64, gp64 = res["f64"]
+    J16, gs16, gq16, gp16 = res["bf16"]
+    scale = max(np.abs(gs64).max(), np.abs(gq64).max(), np.abs(gp64).max())
+    errs = [np.abs(a - b).max() / scale for a, b in ((gs16, gs64), (gq16, gq64), (gp16, gp64))]
+    print("bf16 adjoint: J %.3e vs %.3e, gradient errors %s" % (J16, J64, errs))
+    assert abs(J16 - J64) <= 0.2 * J64
+    assert max(errs) <= 0.2
