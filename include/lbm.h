@@ -133,6 +133,16 @@ int lbm_set_scheme(lbm_ctx *ctx, double c0, double c1, double c2, double b,
 /* Uniform body force g (lattice units, 3 components; g[2] ignored in 2D). */
 int lbm_set_force(lbm_ctx *ctx, const double g[3]);
 
+/* Time-dependent wall velocity of the form phi(x_b, t) = a(t) phi_0(x_b) (Eq. 2.10's
+ * phi evaluated at the time of the step, as in the paper's moving curved wall of
+ * Sec. 3.2, whose field decays uniformly): from the current time t0 on, step t uses
+ * every link's wall velocity (lbm_set_geometry / lbm_set_link_values) times
+ * a(t) = a0 * r^(t - t0).  a0 = r = 1 (the default) is the constant wall.  The
+ * adjoint (lbm_adjoint) follows the same factor step by step.  A batch uses each
+ * member's factor for the member's time at the batch call, held for that call.
+ * Errors: LBM_EINVAL for a non-finite a0 or r <= 0. */
+int lbm_set_wall_factor(lbm_ctx *ctx, double a0, double r);
+
 /* f = f^eq(rho, u) (Eq. 42) on fluid nodes.  rho: nodes doubles or NULL (rho0);
  * u: D*nodes doubles (D = 2 or 3, node-major) or NULL (rest).  Time resets to 0. */
 int lbm_init_equilibrium(lbm_ctx *ctx, const double *rho, const double *u);

@@ -23,7 +23,7 @@ STATUS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA",
 
 # every symbol include/lbm.h declares
 EXPORTS = ["lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_set_skew", "lbm_set_geometry",
-           "lbm_set_scheme", "lbm_set_force", "lbm_init_equilibrium", "lbm_set_populations",
+           "lbm_set_scheme", "lbm_set_force", "lbm_set_wall_factor", "lbm_init_equilibrium", "lbm_set_populations",
            "lbm_get_populations", "lbm_step", "lbm_time", "lbm_moments", "lbm_moments_device",
            "lbm_error_norms", "lbm_error_norms_noalloc", "lbm_query", "lbm_last_error",
            "lbm_set_relaxation", "lbm_set_link_values", "lbm_adjoint",
@@ -49,6 +49,7 @@ def load_library(path=LIB_PATH):
         "lbm_set_geometry": (I, [P, P, I64, P, P, P, P]),
         "lbm_set_scheme": (I, [P, D, D, D, D, I]),
         "lbm_set_force": (I, [P, P]),
+        "lbm_set_wall_factor": (I, [P, D, D]),
         "lbm_init_equilibrium": (I, [P, P, P]),
         "lbm_set_populations": (I, [P, P]),
         "lbm_get_populations": (I, [P, P]),
@@ -160,6 +161,10 @@ class Lbm:
     def set_force(self, g):
         g = np.ascontiguousarray(list(g) + [0.0] * (3 - len(g)), dtype=np.float64)
         self._check(self._lib.lbm_set_force(self.h, _ptr(g)))
+
+    def set_wall_factor(self, a0=1.0, r=1.0):
+        """lbm_set_wall_factor: wall velocities times a0 r^(t - now) at step t."""
+        self._check(self._lib.lbm_set_wall_factor(self.h, float(a0), float(r)))
 
     def init_equilibrium(self, rho=None, u=None):
         rho = None if rho is None else np.ascontiguousarray(np.asarray(rho).reshape(self.N), dtype=np.float64)

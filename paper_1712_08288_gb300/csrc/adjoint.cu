@@ -98,11 +98,11 @@ __global__ void loss_kernel(AuxArgs a, const C *g, const uint8_t *mask, const do
 
 // Link data of the adjoint step.  The gradients with respect to a link's wall
 // fraction q and wall velocity phi are linear in two sums over the steps
-// (Eq. 2.13 differentiated through l(q)):
-//   dJ/dq   = b sum_t lambda_i (A' f_d + B' f'_i + C' f'_d) + b W' sum_t lambda_i,
-//   dJ/dphi = b 2 w_i rho0 e_i / ((1 + l) c_s^2) sum_t lambda_i,
-// with ' = d/dq.  The kernel accumulates only sum_t lambda_i and the first sum, per
-// link and in the compute type; the host folds in the other factors in FP64.
+// (Eq. 2.13 differentiated through l(q); a(t) the step's wall-velocity factor):
+//   dJ/dq   = b sum_t lambda_i (A' f_d + B' f'_i + C' f'_d) + b W' sum_t a(t) lambda_i,
+//   dJ/dphi = b 2 w_i rho0 e_i / ((1 + l) c_s^2) sum_t a(t) lambda_i,
+// with ' = d/dq.  The kernel accumulates only sum_t a(t) lambda_i and the first sum,
+// per link and in the compute type; the host folds in the other factors in FP64.
 struct AdjGeo {
   const void *dcoef;          // LinkCoef<C> per link: (A', B', C', 0)
   void *acc;                  // 2 C per link: sum lambda_i, sum lambda_i (A' g_d + B' g'_i + C' g'_d)
@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(kAdjThreads, sizeof(C) == 4 ? LBM_ADJ_MINB_F32
           // deviations suffice: A' + B' + C' = 0 removes the w_i rho0 parts
           const LinkCoef<C> dc = static_cast<const LinkCoef<C> *>(ag.dcoef)[k];
           C *acc = static_cast<C *>(ag.acc) + 2 * (long long)k;
-          acc[0] += av;
+          acc[0] += av * sa.wfac;           // W and its derivatives carry the step's factor
           acc[1] += av * (dc.a * g[dd] + dc.bb * gp[i] + dc.c * gp[dd]);
         }
       }
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(kAdjThreads, sizeof(C) == 4 ? 6 : 3)
         const LinkCoef<C> c = coef[off + __popc(mask & ((1u << dd) - 1u))];
         const int i = L::opp(dd);
         fout[(long long)i * N + n] =
-            sa.one_minus_b * g[i] + c.a * g[dd] + c.bb * gp[i] + c.c * gp[dd] + c.w;
+            sa.one_minus_b * g[i] + c.a * g[dd] + c.bb * gp[i] + c.c * gp[dd] + c.w * sa.wfac;
       }
     }
   }

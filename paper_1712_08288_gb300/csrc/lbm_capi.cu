@@ -57,6 +57,8 @@ struct lbm_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   long long t = 0;
+  double wf_a0 = 1.0, wf_r = 1.0;  // wall-velocity factor a0 r^(t - wf_t0)
+  long long wf_t0 = 0;
   bool geometry_set = false;
 
   // device buffers
@@ -155,6 +157,16 @@ static AuxArgs aux_args(const lbm_ctx *c) {
   return a;
 }
 
+// wall-velocity factor a0 r^(t - t0) of step t (lbm_set_wall_factor)
+static double wall_factor(const lbm_ctx *c, long long t) {
+  return c->wf_a0 * std::pow(c->wf_r, (double)(t - c->wf_t0));
+}
+static void set_step_factor(lbm_ctx *c, long long t) {
+  const double a = wall_factor(c, t);
+  c->a64.wfac = a;
+  c->a32.wfac = (float)a;
+}
+
 static void refresh_args(lbm_ctx *c) {
   DevGeometry geo;
   geo.cls = c->cls; geo.bidx = c->bidx; geo.bmask = c->bmask; geo.boff = c->boff;
@@ -179,6 +191,7 @@ static void refresh_args(lbm_ctx *c) {
     });
     a.inv_rho0 = C(1.0 / c->rho0);
     a.one_minus_b = C(1.0 - c->b);
+    a.wfac = C(wall_factor(c, c->t));
     a.status = c->status;
     with_lat(c->lattice, [&](auto lat) {
       using L = decltype(lat);
@@ -569,6 +582,18 @@ int lbm_set_scheme(lbm_ctx *c, double c0, double c1, double c2, double b, int al
   return rc;
 }
 
+int lbm_set_wall_factor(lbm_ctx *c, double a0, double r) {
+  if (!c) return LBM_EINVAL;
+  if (!std::isfinite(a0) || !std::isfinite(r) || !(r > 0))
+    return fail(c, LBM_EINVAL, "lbm_set_wall_factor: need finite a0 and r > 0");
+  c->wf_a0 = a0;
+  c->wf_r = r;
+  c->wf_t0 = c->t;
+  set_step_factor(c, c->t);
+  ++c->version;   // batches take the factor of the member's time at each batch call
+  return LBM_OK;
+}
+
 int lbm_set_force(lbm_ctx *c, const double g[3]) {
   if (!c || !g) return LBM_EINVAL;
   for (int k = 0; k < 3; ++k)
@@ -637,6 +662,7 @@ int lbm_step(lbm_ctx *c, int n) {
   if (n < 0) return fail(c, LBM_EINVAL, "lbm_step: n = %d < 0", n);
   if (!c->geometry_set) return fail(c, LBM_ESTATE, "lbm_step: geometry not set");
   for (int k = 0; k < n; ++k) {
+    set_step_factor(c, c->t);
     const cudaError_t e = launch_sweep(c->lattice, c->precision, (c->t & 1) != 0, c->a64, c->a32,
                                        c->tiles, c->n_tiles, c->bx, c->stream);
     if (e != cudaSuccess) return fail(c, LBM_ECUDA, "lbm_step: %s", cudaGetErrorString(e));
@@ -905,9 +931,11 @@ int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *ma
     };
     if (!last) {
       if (natural) {
-        for (int r = 0; r + 1 < len; ++r)
+        for (int r = 0; r + 1 < len; ++r) {
+          set_step_factor(c, tck[sgm] + r);
           ADJ_CUDA(launch_recompute_step(c->lattice, c->precision, c->a64, c->a32, aux_args(c),
                                          at(r), at(r + 1), st));
+        }
       } else {
         ADJ_CUDA(load_raw(ck + ck_bytes * sgm));
         c->t = tck[sgm];
@@ -915,6 +943,7 @@ int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *ma
       }
     }
     for (int r = len - 1; r >= 0; --r) {
+      set_step_factor(c, tck[sgm] + r);
       ADJ_CUDA(launch_adjoint_step(c->lattice, c->precision, c->a64, c->a32, aux_args(c), dcoef,
                                    acc, at(r), lin, lout, gpart, st));
       std::swap(lin, lout);

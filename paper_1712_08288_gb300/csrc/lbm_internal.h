@@ -81,6 +81,7 @@ struct SweepArgs {
   C F[3];                    // rho0 g / |M_j|^2
   C inv_rho0;
   C one_minus_b;
+  C wfac;                    // factor on every link's wall velocity in this step
   int *status;               // bit 0: non-finite density seen, bit 1: bounded wait gave up
   // element offsets of the stores of an interior node: even step slot opp(i) of
   // the node itself, odd step slot i of x + e_i (no wrap)

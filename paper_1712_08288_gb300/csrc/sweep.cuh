@@ -621,7 +621,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
           const int kk = boff + __popc(bmask & ((1u << dd) - 1u));
           const LinkCoef<C> c = coef[kk];
           const int i = L::opp(dd);
-          const C v = A.one_minus_b * g[i] + c.a * g[dd] + c.bb * gp[i] + c.c * gp[dd] + c.w;
+          const C v = A.one_minus_b * g[i] + c.a * g[dd] + c.bb * gp[i] + c.c * gp[dd] + c.w * A.wfac;
           if (!ODD) Storage<T>::store(lnk + kk, v);          // read by the next odd step
           else Storage<T>::store(pn + (I)i * S, v);          // slot i of x_f itself
         }

@@ -188,6 +188,61 @@ def couette_config(n):
     return w
 
 
+def taylor_green_disc(inv_h, s_nu, nu=0.002, U0=0.05, rho0=1.0, lattice="D2Q9"):
+    """The paper's Taylor-Green vortex in the disc (x - 1/2)^2 + (y - 1/2)^2 <= 1/16
+    (Sec. 3.2): nu = 0.002, U0 = 0.05, p0 = rho0 c_s^2, h = 1/inv_h, delta_t = eta h^2
+    with eta = (1/s_nu - 1/2)/(3 nu), no force.
+
+    Node (i, j) sits at (i h, j h), i, j = 0..inv_h; nodes outside the disc or on its
+    rim are solid.  Lattice-unit outputs: the analytic velocity scales by eta h, the
+    pressure by (eta h)^2, and rho = rho0 + (p - p0)/c_s^2.  The wall velocity of a
+    link is the analytic velocity at its wall point x_b = x_f + q e_d at t = 0; the
+    whole field decays as exp(-8 pi^2 nu t), so at step n it is the t = 0 value times
+    decay**n (decay = exp(-8 pi^2 nu eta h^2)).  T = 1/U0 is `steps` steps (rounded).
+    """
+    n = int(inv_h) + 1
+    h = 1.0 / inv_h
+    shape = (n, n, 1)
+    E = DIRECTIONS[lattice]
+    x, y, z = _coords(shape)
+    X, Y = x * h, y * h
+    R = 0.25
+    # in units of h the disc is 4((2i - m)^2 + (2j - m)^2) < m^2 with m = inv_h: an
+    # exact integer test, so nodes on the rim are solid
+    m = int(inv_h)
+    solid = ~(4 * ((2 * x - m) ** 2 + (2 * y - m) ** 2) < m * m)
+    node, d = cut_links(lattice, shape, (0, 0), solid)
+    px, py = X[node], Y[node]
+    dx = E[d, 0].astype(np.float64) * h
+    dy = E[d, 1].astype(np.float64) * h
+    wx, wy = px - 0.5, py - 0.5
+    q = _first_root(dx * dx + dy * dy, 2 * (dx * wx + dy * wy), wx * wx + wy * wy - R * R)
+    xb, yb = px + q * dx, py + q * dy
+    eta = (1.0 / s_nu - 0.5) / (3.0 * nu)
+    vs = eta * h                                   # physical -> lattice velocity
+
+    def vel(xx, yy):
+        return (-U0 * np.cos(2 * np.pi * xx) * np.sin(2 * np.pi * yy),
+                U0 * np.cos(2 * np.pi * yy) * np.sin(2 * np.pi * xx))
+
+    uw = np.zeros((len(node), 3))
+    ub, vb = vel(xb, yb)
+    uw[:, 0], uw[:, 1] = ub * vs, vb * vs
+    u0 = np.full((x.size, 3), np.nan)
+    fl = ~solid
+    ux, uy = vel(X, Y)
+    u0[fl, 0], u0[fl, 1], u0[fl, 2] = ux[fl] * vs, uy[fl] * vs, 0.0
+    dp = -0.25 * U0 * U0 * (np.cos(4 * np.pi * X) + np.cos(4 * np.pi * Y)) * vs * vs
+    rho = np.where(fl, rho0 + 3.0 * dp, rho0)
+    dt = eta * h * h
+    decay = float(np.exp(-8 * np.pi ** 2 * nu * dt))
+    steps = int(round((1.0 / U0) / dt))
+    return dict(lattice=lattice, shape=shape, skew=(0, 0), solid=solid,
+                links=dict(node=node, d=d, q=q, uw=uw), u_exact=u0, rho_init=rho,
+                decay=decay, steps=steps, force=(0.0, 0.0, 0.0),
+                S=relaxation_rates(lattice, s_nu), rho0=rho0, s_nu=s_nu)
+
+
 def poiseuille_2d(Ny, gamma, s_nu, nx=2, nu_phys=0.03, lattice="D2Q9"):
     """The paper's Poiseuille channel (Sec. 3.1): rows j = 0 and j = Ny are solid, rows
     1..Ny-1 are fluid, the walls sit a fraction gamma of a link outside rows 1 and

@@ -89,3 +89,88 @@ def test_poiseuille_parameter_grid_second_order(s_nu):
         if not 1.8 < p < 2.5:
             bad[(r, gm)] = (e, p)
     assert not bad, bad
+
+
+def _tg_gpu(w, rule, prec="f64"):
+    sim = gpu_sim(w, prec, scheme=RULES[rule] + (1.0,))
+    sim.init_equilibrium(w["rho_init"], np.nan_to_num(w["u_exact"]))
+    sim.set_wall_factor(1.0, w["decay"])
+    return sim
+
+
+def test_taylor_green_moving_wall_matches_oracle():
+    """The moving curved wall of Sec. 3.2 (wall velocity decaying every step through
+    lbm_set_wall_factor) against the oracle with phi(x_b, t) reset before each step."""
+    from oracle import lattices as OL
+    from oracle import lbm as O
+    from gpu_common import deviation, rel_err
+    w = W.taylor_green_disc(40, 1.0)
+    o = O.Simulation(OL.D2Q9, w["shape"], w["S"], 1.0, w["solid"], w["links"],
+                     scheme=RULES["g2+g"] + (1.0,))
+    o.init_equilibrium(w["rho_init"], np.nan_to_num(w["u_exact"])[:, :2])
+    uw0 = w["links"]["uw"].copy()
+    steps = 61
+    for n in range(steps):
+        o.link_uw = uw0 * w["decay"] ** n
+        o.step()
+    g = _tg_gpu(w, "g2+g")
+    g.step(steps)
+    fl = ~w["solid"]
+    assert rel_err(deviation(g.get_populations(), OL.D2Q9), deviation(o.f, OL.D2Q9), fl) < 1e-12
+
+
+@pytest.mark.parametrize("s_nu", [0.5, 1.0, 1.5, 1.99])
+def test_taylor_green_disc_second_order(s_nu):
+    """Sec. 3.2: E_r at T = 1/U0 for h = 1/40 and 1/80, all five l-rules; second
+    order (ratio of errors about 4) at every s_nu including 1.99."""
+    bad = {}
+    for rule in RULES:
+        e = []
+        for inv_h in (40, 80):
+            w = W.taylor_green_disc(inv_h, s_nu)
+            sim = _tg_gpu(w, rule)
+            sim.step(w["steps"])
+            ue = np.nan_to_num(w["u_exact"]) * w["decay"] ** w["steps"]
+            e.append(sim.error_norms(ue)["l2_rel"])
+        p = np.log(e[0] / e[1]) / np.log(2)
+        print("TG s_nu %.2f rule %-5s E_r %s order %.2f" % (s_nu, rule, e, p))
+        if not 1.7 < p < 2.8:
+            bad[rule] = (e, p)
+    assert not bad, bad
+
+
+def test_adjoint_follows_the_wall_factor():
+    """dJ/dq and dJ/dphi with a decaying wall velocity against central differences
+    of the forward run (FP64)."""
+    w = W.taylor_green_disc(40, 1.0)
+    N = w["shape"][0] * w["shape"][1]
+    rng = np.random.default_rng(31)
+    mask = rng.random(N) < 0.5
+    ut = np.zeros((N, 2))
+    steps = 40
+
+    def run(q=None, uw=None, grad=False):
+        sim = gpu_sim(w, "f64", scheme=RULES["g"] + (1.0,))
+        if q is not None or uw is not None:
+            sim.set_link_values(q, uw)
+        sim.init_equilibrium(w["rho_init"], np.nan_to_num(w["u_exact"]))
+        sim.set_wall_factor(1.0, w["decay"] ** 20)      # a strong decay to test the weighting
+        return sim.adjoint(steps, mask, ut)
+
+    J, gs, gq, gp = run()
+    q0 = w["links"]["q"].copy()
+    uw0 = w["links"]["uw"].copy()
+    scale = max(np.abs(gq).max(), np.abs(gp).max())
+    h = 1e-6
+    for k in rng.choice(len(q0), 3, replace=False):
+        qp, qm = q0.copy(), q0.copy()
+        qp[k] = min(q0[k] + h, 1.0)
+        qm[k] = q0[k] - h
+        fd = (run(q=qp)[0] - run(q=qm)[0]) / (qp[k] - qm[k])
+        assert abs(fd - gq[k]) <= 1e-5 * scale
+        for a in range(2):
+            up, um = uw0.copy(), uw0.copy()
+            up[k, a] += h
+            um[k, a] -= h
+            fd = (run(uw=up)[0] - run(uw=um)[0]) / (2 * h)
+            assert abs(fd - gp[k, a]) <= 1e-5 * scale

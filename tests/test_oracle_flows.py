@@ -97,3 +97,27 @@ def test_tilted_pipe_order_d3q19():
         _, u = sim.moments()
         errs.append(O.relative_l2_error(w["u_exact"], u, ~w["solid"]))
     assert 1.85 < np.log2(errs[0] / errs[1]) < 2.3, errs
+
+
+def taylor_green_error(inv_h, s_nu, rule):
+    """E_r at T = 1/U0 of the Taylor-Green vortex in the disc (Sec. 3.2), analytic
+    start (rho from the pressure, u), the wall velocity phi(x_b, t) of every link set
+    to the analytic value at the start of each step."""
+    w = W.taylor_green_disc(inv_h, s_nu)
+    sim = O.Simulation(L.D2Q9, w["shape"], w["S"], 1.0, w["solid"], w["links"],
+                       scheme=RULES[rule] + (1.0,))
+    sim.init_equilibrium(w["rho_init"], np.nan_to_num(w["u_exact"])[:, :2])
+    uw0 = w["links"]["uw"].copy()
+    for n in range(w["steps"]):
+        sim.link_uw = uw0 * w["decay"] ** n
+        sim.step()
+    _, u = sim.moments()
+    ue = np.nan_to_num(w["u_exact"])[:, :2] * w["decay"] ** w["steps"]
+    return O.relative_l2_error(ue, u[:, :2], ~w["solid"])
+
+
+def test_taylor_green_disc_order():
+    """Moving curved wall (Sec. 3.2): h = 1/40 -> 1/80 at s_nu = 1 reduces E_r by ~4."""
+    e = [taylor_green_error(n, 1.0, "g") for n in (40, 80)]
+    p = np.log(e[0] / e[1]) / np.log(2)
+    assert e[1] < 1e-3 and 1.8 < p < 2.6, (e, p)
