@@ -293,6 +293,11 @@ def run_gpu(args):
     if args.refine_max > 0 and rank == 0:
         ref = run_refinement(args, torch, stream)
 
+    # ---- moving curved wall: Taylor-Green in a disc (order of convergence) ------
+    tg = None
+    if args.tg_max > 0 and rank == 0:
+        tg = run_taylor_green(args, torch, stream)
+
     # ---- adjoint: gradients through the whole run, sqrt(N) checkpointing --------
     adj = None
     if args.adjoint_steps > 0 and rank == 0:
@@ -326,6 +331,7 @@ def run_gpu(args):
             "accuracy": acc,
             "ensemble": ens,
             "refinement": ref,
+            "taylor_green": tg,
             "adjoint": adj,
             "e2e": e2e,
             "gpu_launches": args.steps,
@@ -449,6 +455,34 @@ def run_refinement(args, torch, stream):
             out[prec + "_mlups_at_n"] = round(nf * k / (total * 1e-3) / 1e6, 1)
             del sim
     out["workload"] = "D2Q9 circular Couette, 64^2 configuration scaled to n (diffusive scaling)"
+    return out
+
+
+def run_taylor_green(args, torch, stream):
+    """The paper's Taylor-Green vortex in a disc (Sec. 3.2; D2Q9, moving curved wall
+    through lbm_set_wall_factor, l = gamma): E_r at T = 1/U0 for h = 1/40 .. 1/200 at
+    s_nu = 1 and 1.99, FP64, and the least-squares order."""
+    from paper_1712_08288_gb300 import workloads as W
+    sizes = [n for n in (40, 80, 120, 160, 200) if n <= args.tg_max]
+    out = {"workload": "Taylor-Green vortex in the disc of Sec. 3.2, nu 0.002, U0 0.05, T = 1/U0",
+           "inv_h": sizes}
+    t_start = time.perf_counter()
+    for s_nu in (1.0, 1.99):
+        errs, steps = [], []
+        for n in sizes:
+            w = W.taylor_green_disc(n, s_nu)
+            sim = build_sim(w, "f64", torch, stream)
+            sim.init_equilibrium(w["rho_init"], np.nan_to_num(w["u_exact"]))
+            sim.set_wall_factor(1.0, w["decay"])
+            sim.step(w["steps"])
+            ue = np.nan_to_num(w["u_exact"]) * w["decay"] ** w["steps"]
+            errs.append(sim.error_norms(ue, check=False)["l2_rel"])
+            steps.append(w["steps"])
+            del sim
+        # slope of log E_r against log h
+        order = float(np.polyfit(np.log(1.0 / np.array(sizes)), np.log(errs), 1)[0]) if len(sizes) > 1 else None
+        out["s_nu_%g" % s_nu] = {"E_r": errs, "steps": steps, "order": order}
+    out["seconds"] = round(time.perf_counter() - t_start, 1)
     return out
 
 
@@ -593,6 +627,7 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--d3q15-steps", type=int, default=1000)
     ap.add_argument("--refine-max", type=int, default=512)
+    ap.add_argument("--tg-max", type=int, default=200)
     ap.add_argument("--refine-max-steps", type=int, default=600000)
     ap.add_argument("--refine-mlups-n", type=int, default=2048)
     ap.add_argument("--ensemble-count", type=int, default=96)
