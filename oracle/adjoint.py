@@ -72,6 +72,7 @@ def _boundary_partials(sim, k, fi, fd, pi, pd):
 def adjoint(sim, n_steps, mask, u_target):
     """Run n_steps forward from sim's current state and return
     (J, dJ/ds (Q,), dJ/dq (links,), dJ/dphi (links, 3)).  sim ends advanced."""
+    assert not getattr(sim, "two_node", False), "the adjoint follows the single-node scheme"
     lat = sim.lat
     Q, N = lat.Q, sim.N
     fl = sim.fluid

@@ -129,16 +129,20 @@ def is_convex(gamma, l):
 
 
 def boundary_value(w_i, e_i, gamma, l, b, rho0, phi,
-                   f_i_t, f_ibar_t, fpost_i, fpost_ibar):
+                   f_i_t, f_ibar_t, fpost_i, fpost_ibar, f_ibar_next=None):
     """f_i(x_f, t+1) for one cut link, following Sec. 2 step by step.
 
     Inputs are the boundary node's own populations: f_i(x_f,t), f_ibar(x_f,t)
     (pre-collision) and f'_i(x_f,t), f'_ibar(x_f,t) (post-collision).  Every
     argument may also be an array over links (e_i and phi then have a last axis
     of length 3), in which case the formula is applied link by link.
+    f_ibar_next: the two-node scheme (Remark (2) after Eq. 2.10, Eq. 2.11) passes
+    the exact f_ibar(x_f, t+dt) = f'_ibar(x_l, t) of the fluid neighbour x_l here;
+    None keeps the single-node approximation.
     """
-    # Eq. (2.9): f_ibar(x_f, t+dt) ~ f_ibar(x_f, t)
-    f_ibar_next = f_ibar_t
+    if f_ibar_next is None:
+        # Eq. (2.9): f_ibar(x_f, t+dt) ~ f_ibar(x_f, t)
+        f_ibar_next = f_ibar_t
     # Eq. (2.7): interpolation at x_2 between x_f (t+dt) and x_r, whose value at
     # t+dt is the advected f'_ibar(x_f, t)
     f_ibar_x2 = (1 + l - 2 * gamma) * f_ibar_next + (2 * gamma - l) * fpost_ibar
@@ -164,7 +168,7 @@ class Simulation:
     """
 
     def __init__(self, lat, shape, S, rho0, solid, links, scheme=(0.0, 1.0, 0.0, 1.0),
-                 force=(0.0, 0.0, 0.0), skew=(0, 0)):
+                 force=(0.0, 0.0, 0.0), skew=(0, 0), two_node=False):
         self.lat = lat
         self.shape = tuple(int(s) for s in shape)
         self.N = self.shape[0] * self.shape[1] * self.shape[2]
@@ -196,6 +200,9 @@ class Simulation:
         assert np.all((q > 0) & (q <= 1)), "gamma must lie in (0, 1] (Sec. 2)"
         self.link_node, self.link_d, self.link_q, self.link_uw = node, d, q, uw
         self.link_l = l_of_gamma(q, c0, c1, c2)
+        # two-node scheme (Eq. 2.11) on the links whose x_l = x_f + e_i is fluid
+        self.two_node = bool(two_node)
+        self.link_xl = self.nbr[lat.opp[d], node] if len(node) else np.zeros(0, np.int64)
         assert np.all(self.link_l >= 0), "l must be non-negative (Sec. 2)"
 
         self.f = np.full((lat.Q, self.N), np.nan)
@@ -245,9 +252,13 @@ class Simulation:
         n = self.link_node
         d = self.link_d
         i = lat.opp[d]
+        nxt = None
+        if self.two_node:
+            xl = self.link_xl
+            nxt = np.where(fl[xl], fpost[d, xl], f[d, n])    # x_l solid: Eq. (2.9)
         fnew[i, n] = boundary_value(
             lat.w[i], lat.e[i], self.link_q, self.link_l, self.b, self.rho0,
-            self.link_uw, f[i, n], f[d, n], fpost[i, n], fpost[d, n])
+            self.link_uw, f[i, n], f[d, n], fpost[i, n], fpost[d, n], nxt)
         assert not np.isnan(fnew[:, fl]).any(), "a fluid population was not written"
         self.f = fnew
         self.t += 1

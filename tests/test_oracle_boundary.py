@@ -164,3 +164,33 @@ def test_half_way_closed_channel_conserves_mass():
     m0 = sim.mass()
     sim.step(30)
     assert abs(sim.mass() - m0) < 1e-13 * m0
+
+
+def test_two_node_yms2003_special_case():
+    """Remark (4): with l = gamma the two-node scheme (Eq. 2.11) is the scheme of Yu,
+    Mei & Shyy (2003): (1-g)/(1+g) f'_ibar(x_l) + g/(1+g) [f'_i + f'_ibar] +
+    2/(1+g) w rho0 e.phi/c_s^2 -- the exact f_ibar(x_f, t+1) = f'_ibar(x_l, t) takes
+    the place of Eq. (2.9)'s f_ibar(x_f, t)."""
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        g = rng.uniform(0.01, 1.0)
+        fi, fib, pi, pib, pl = rng.uniform(0, 0.2, 5)
+        phi = 0.05 * rng.standard_normal(3)
+        e = np.array([0, 1, -1])
+        w = 1 / 36
+        got = O.boundary_value(w, e, g, g, 1.0, RHO0, phi, fi, fib, pi, pib, f_ibar_next=pl)
+        want = ((1 - g) / (1 + g) * pl + g / (1 + g) * (pi + pib)
+                + 2 / (1 + g) * w * RHO0 * (e @ phi) * 3)
+        assert abs(got - want) < 1e-15
+
+
+def test_two_node_equals_single_node_for_halfway_bounce_back():
+    """gamma = 1/2, l = 0: the weight of f_ibar(x_f, t+1) is (1 + l - 2 gamma)/(1 + l)
+    = 0, so both schemes give half-way bounce-back whatever x_l holds."""
+    rng = np.random.default_rng(2)
+    fi, fib, pi, pib, pl = rng.uniform(0, 0.2, 5)
+    phi = np.array([0.01, -0.02, 0.0])
+    e = np.array([1, 0, 0])
+    a = O.boundary_value(1 / 9, e, 0.5, 0.0, 1.0, RHO0, phi, fi, fib, pi, pib)
+    b = O.boundary_value(1 / 9, e, 0.5, 0.0, 1.0, RHO0, phi, fi, fib, pi, pib, f_ibar_next=pl)
+    assert a == b

@@ -36,10 +36,10 @@ def observed_order(sizes, errors):
     return -np.polyfit(np.log(sizes), np.log(errors), 1)[0]
 
 
-def poiseuille_error(Ny, gamma, s_nu, rule, b=1.0):
+def poiseuille_error(Ny, gamma, s_nu, rule, b=1.0, two_node=False):
     w = W.poiseuille_2d(Ny, gamma, s_nu)
     sim = O.Simulation(L.D2Q9, w["shape"], w["S"], w["rho0"], w["solid"], w["links"],
-                       scheme=RULES[rule] + (b,), force=w["force"])
+                       scheme=RULES[rule] + (b,), force=w["force"], two_node=two_node)
     sim.init_equilibrium(None, np.nan_to_num(w["u_exact"])[:, :2])
     run_to_steady(sim, 1e-11)
     _, u = sim.moments()
@@ -121,3 +121,13 @@ def test_taylor_green_disc_order():
     e = [taylor_green_error(n, 1.0, "g") for n in (40, 80)]
     p = np.log(e[0] / e[1]) / np.log(2)
     assert e[1] < 1e-3 and 1.8 < p < 2.6, (e, p)
+
+
+@pytest.mark.parametrize("rule,gamma", [("g", 0.25), ("g2+g", 0.75), ("2g", 1.0)])
+def test_two_node_scheme_is_second_order(rule, gamma):
+    """Eq. (2.11) (Remark (2)): the two-node variant keeps second order on the
+    Poiseuille channel."""
+    sizes = [11, 21, 41]
+    errs = [poiseuille_error(n, gamma, 1.0, rule, two_node=True) for n in sizes]
+    inv_h = [n - 2 + 2 * gamma for n in sizes]
+    assert 1.85 < observed_order(inv_h, errs) < 2.4, errs
