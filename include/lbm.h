@@ -133,6 +133,16 @@ int lbm_set_scheme(lbm_ctx *ctx, double c0, double c1, double c2, double b,
 /* Uniform body force g (lattice units, 3 components; g[2] ignored in 2D). */
 int lbm_set_force(lbm_ctx *ctx, const double g[3]);
 
+/* Two-node variant of the scheme (Sec. 2, Remark (2), Eq. 2.11): enable != 0 makes
+ * every cut link whose node behind the boundary node, x_l = x_f + e_i, is fluid use
+ * the exact f_ibar(x_f, t+1) = f'_ibar(x_l, t) in place of Eq. 2.9's f_ibar(x_f, t)
+ * (within Eq. 2.13's b-combination); links with a solid x_l keep Eq. 2.10.  With
+ * l = gamma this is the scheme of Yu, Mei & Shyy (2003) (Remark (4)).  Each step then
+ * runs a small pass over those links before and after the sweep.  Stays on across
+ * lbm_set_geometry.  lbm_adjoint and batches need it off (LBM_ESTATE).
+ * Errors: LBM_ESTATE before lbm_set_geometry. */
+int lbm_set_two_node(lbm_ctx *ctx, int enable);
+
 /* Time-dependent wall velocity of the form phi(x_b, t) = a(t) phi_0(x_b) (Eq. 2.10's
  * phi evaluated at the time of the step, as in the paper's moving curved wall of
  * Sec. 3.2, whose field decays uniformly): from the current time t0 on, step t uses

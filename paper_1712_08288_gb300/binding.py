@@ -23,7 +23,7 @@ STATUS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA",
 
 # every symbol include/lbm.h declares
 EXPORTS = ["lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_set_skew", "lbm_set_geometry",
-           "lbm_set_scheme", "lbm_set_force", "lbm_set_wall_factor", "lbm_init_equilibrium", "lbm_set_populations",
+           "lbm_set_scheme", "lbm_set_force", "lbm_set_wall_factor", "lbm_set_two_node", "lbm_init_equilibrium", "lbm_set_populations",
            "lbm_get_populations", "lbm_step", "lbm_time", "lbm_moments", "lbm_moments_device",
            "lbm_error_norms", "lbm_error_norms_noalloc", "lbm_query", "lbm_last_error",
            "lbm_set_relaxation", "lbm_set_link_values", "lbm_adjoint",
@@ -50,6 +50,7 @@ def load_library(path=LIB_PATH):
         "lbm_set_scheme": (I, [P, D, D, D, D, I]),
         "lbm_set_force": (I, [P, P]),
         "lbm_set_wall_factor": (I, [P, D, D]),
+        "lbm_set_two_node": (I, [P, I]),
         "lbm_init_equilibrium": (I, [P, P, P]),
         "lbm_set_populations": (I, [P, P]),
         "lbm_get_populations": (I, [P, P]),
@@ -161,6 +162,10 @@ class Lbm:
     def set_force(self, g):
         g = np.ascontiguousarray(list(g) + [0.0] * (3 - len(g)), dtype=np.float64)
         self._check(self._lib.lbm_set_force(self.h, _ptr(g)))
+
+    def set_two_node(self, enable=True):
+        """lbm_set_two_node: Eq. 2.11 on the links whose x_l is fluid."""
+        self._check(self._lib.lbm_set_two_node(self.h, int(bool(enable))))
 
     def set_wall_factor(self, a0=1.0, r=1.0):
         """lbm_set_wall_factor: wall velocities times a0 r^(t - now) at step t."""

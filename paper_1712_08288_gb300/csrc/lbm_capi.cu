@@ -60,6 +60,10 @@ struct lbm_ctx {
   double wf_a0 = 1.0, wf_r = 1.0;  // wall-velocity factor a0 r^(t - wf_t0)
   long long wf_t0 = 0;
   bool geometry_set = false;
+  bool two_node = false;        // Eq. 2.11 on links whose x_l is fluid
+  TwoNodeLink *tn = nullptr;
+  long long n_tn = 0;
+  void *tn_delta = nullptr;
 
   // device buffers
   void *pop_alloc = nullptr;    // populations with kPopPadBytes on both sides
@@ -84,6 +88,7 @@ struct lbm_ctx {
 
   // host copy of the cut links in device order (for re-deriving coefficients)
   std::vector<int32_t> link_dir;
+  std::vector<int64_t> link_node;
   std::vector<double> link_q;
   std::vector<double> link_uw;  // 3 per link
   std::vector<int64_t> link_src; // input position of the link at each device position
@@ -256,7 +261,43 @@ static int upload_coefficients(lbm_ctx *c) {
   return LBM_OK;
 }
 
+static void free_two_node(lbm_ctx *c) {
+  cudaFree(c->tn); c->tn = nullptr;
+  cudaFree(c->tn_delta); c->tn_delta = nullptr;
+  c->n_tn = 0;
+}
+
+// device list of the links whose node behind the boundary node, x_l = x_f + e_i,
+// is fluid (the others keep the single-node value)
+static int build_two_node(lbm_ctx *c) {
+  free_two_node(c);
+  if (!c->two_node || c->n_links == 0) return LBM_OK;
+  std::vector<uint8_t> cls(c->N);
+  CUDA_OR_FAIL(c, cudaMemcpy(cls.data(), c->cls, c->N, cudaMemcpyDeviceToHost));
+  std::vector<TwoNodeLink> h;
+  with_lat(c->lattice, [&](auto lat) {
+    using L = decltype(lat);
+    for (long long k = 0; k < c->n_links; ++k) {
+      const long long n = c->link_node[k];
+      const int d = c->link_dir[k], i = L::opp(d);
+      const int x = (int)(n % c->nx);
+      const long long r = n / c->nx;
+      const long long xl = wrap_host(c, x, (int)(r % c->ny), (int)(r / c->ny), L::ex(i), L::ey(i), L::ez(i));
+      if (cls[xl] != kSolid) h.push_back(TwoNodeLink{n, xl, (int)k, d});
+    }
+    return 0;
+  });
+  c->n_tn = (long long)h.size();
+  if (h.empty()) return LBM_OK;
+  CUDA_OR_FAIL(c, cudaMalloc((void **)&c->tn, sizeof(TwoNodeLink) * h.size()));
+  CUDA_OR_FAIL(c, cudaMemcpy(c->tn, h.data(), sizeof(TwoNodeLink) * h.size(), cudaMemcpyHostToDevice));
+  CUDA_OR_FAIL(c, cudaMalloc(&c->tn_delta, (c->precision == LBM_F64 ? 8 : 4) * h.size()));
+  return LBM_OK;
+}
+
+
 static void free_geometry(lbm_ctx *c) {
+  free_two_node(c);
   cudaFree(c->bidx); c->bidx = nullptr;
   cudaFree(c->bmask); c->bmask = nullptr;
   cudaFree(c->boff); c->boff = nullptr;
@@ -507,6 +548,7 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *solid, int64_t n_links, const in
     }
   }
   c->link_dir.assign(n_links, 0);
+  c->link_node.assign(n_links, 0);
   c->link_q.assign(n_links, 0.0);
   c->link_uw.assign(3 * n_links, 0.0);
   c->link_src.assign(n_links, 0);
@@ -515,6 +557,7 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *solid, int64_t n_links, const in
     const int d = dir[k];
     const long long pos = boff[bidx[n]] + __builtin_popcount(mask[n] & ((1u << d) - 1u));
     c->link_dir[pos] = d;
+    c->link_node[pos] = n;
     c->link_src[pos] = k;
     c->link_q[pos] = q[k];
     if (uw)
@@ -551,7 +594,16 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *solid, int64_t n_links, const in
   c->t = 0;
   c->geometry_set = true;
   refresh_args(c);
-  return LBM_OK;
+  return build_two_node(c);
+}
+
+int lbm_set_two_node(lbm_ctx *c, int enable) {
+  if (!c) return LBM_EINVAL;
+  if (!c->geometry_set) return fail(c, LBM_ESTATE, "lbm_set_two_node: geometry not set");
+  cudaSetDevice(c->device);
+  c->two_node = enable != 0;
+  ++c->version;
+  return build_two_node(c);
 }
 
 int lbm_set_scheme(lbm_ctx *c, double c0, double c1, double c2, double b, int allow_nonconvex) {
@@ -663,8 +715,17 @@ int lbm_step(lbm_ctx *c, int n) {
   if (!c->geometry_set) return fail(c, LBM_ESTATE, "lbm_step: geometry not set");
   for (int k = 0; k < n; ++k) {
     set_step_factor(c, c->t);
-    const cudaError_t e = launch_sweep(c->lattice, c->precision, (c->t & 1) != 0, c->a64, c->a32,
-                                       c->tiles, c->n_tiles, c->bx, c->stream);
+    const bool odd = (c->t & 1) != 0;
+    cudaError_t e = cudaSuccess;
+    if (c->n_tn)
+      e = launch_two_node(c->lattice, c->precision, c->a64, c->a32, aux_args(c), odd, false, c->tn,
+                          c->n_tn, c->tn_delta, c->stream);
+    if (e == cudaSuccess)
+      e = launch_sweep(c->lattice, c->precision, odd, c->a64, c->a32, c->tiles, c->n_tiles, c->bx,
+                       c->stream);
+    if (e == cudaSuccess && c->n_tn)
+      e = launch_two_node(c->lattice, c->precision, c->a64, c->a32, aux_args(c), odd, true, c->tn,
+                          c->n_tn, c->tn_delta, c->stream);
     if (e != cudaSuccess) return fail(c, LBM_ECUDA, "lbm_step: %s", cudaGetErrorString(e));
     ++c->t;
   }
@@ -796,6 +857,8 @@ int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *ma
   if (n_steps < 1) return fail(c, LBM_EINVAL, "lbm_adjoint: n_steps >= 1");
   if (!mask || !u_target) return fail(c, LBM_EINVAL, "lbm_adjoint: mask and u_target are required");
   if (checkpoint_every < 0) return fail(c, LBM_EINVAL, "lbm_adjoint: checkpoint_every < 0");
+  if (c->two_node)
+    return fail(c, LBM_ESTATE, "lbm_adjoint: differentiates the single-node scheme; two-node is on");
   if (!c->geometry_set) return fail(c, LBM_ESTATE, "lbm_adjoint: geometry not set");
   cudaSetDevice(c->device);
   const long long T = n_steps;
@@ -1162,6 +1225,7 @@ static int batch_check_parity(lbm_batch *b, bool *odd) {
   const long long t0 = b->ctx[0]->t;
   for (lbm_ctx *c : b->ctx) {
     if (!c->geometry_set) return bfail(b, LBM_ESTATE, "a context of the batch has no geometry");
+    if (c->two_node) return bfail(b, LBM_ESTATE, "batches run the single-node scheme; a member has two-node on");
     if ((c->t & 1) != (t0 & 1))
       return bfail(b, LBM_ESTATE, "contexts of a batch must be at the same time parity");
   }

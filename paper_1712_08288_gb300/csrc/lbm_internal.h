@@ -141,6 +141,19 @@ cudaError_t launch_import_state(int lattice, int precision, const AuxArgs &a, co
 cudaError_t launch_loss(int lattice, int precision, const AuxArgs &a, const void *g,
                         const uint8_t *mask, const double *u_target, void *lam, double *J,
                         cudaStream_t st);
+// a cut link that takes the two-node scheme (Eq. 2.11): boundary node x_f, its
+// fluid neighbour x_l = x_f + e_i behind it, link index k, wall direction d
+struct TwoNodeLink {
+  long long xf, xl;
+  int k, d;
+};
+// pre (post = false): difference of the two schemes for every listed link into
+// delta, from the state at time t (parity odd); post: add it to the values the
+// step t -> t+1 wrote
+cudaError_t launch_two_node(int lattice, int precision, const SweepArgs<double> &a64,
+                            const SweepArgs<float> &a32, const AuxArgs &a, bool odd, bool post,
+                            const TwoNodeLink *tn, long long n_tn, void *delta, cudaStream_t st);
+
 // one step of the adjoint sweep: lambda(t) from lambda(t+1) and the pre-collision
 // state f (natural layout, compute type); per-link sums into link_acc (2 compute-type
 // values per link), dJ/ds into the per-block partial records
