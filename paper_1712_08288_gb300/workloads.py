@@ -69,6 +69,29 @@ def relaxation_rates(lattice, s_nu):
     return np.array(s, dtype=np.float64)
 
 
+def relaxation_rates_bgk(lattice, s):
+    """BGK (single relaxation time) as an MRT vector: every non-conserved moment
+    relaxes at s (the conserved rows' rates have no effect)."""
+    Q = len(DIRECTIONS[lattice])
+    return np.full(Q, float(s))
+
+
+def relaxation_rates_trt(lattice, s_plus, magic=3.0 / 16.0):
+    """Two-relaxation-time collision as an MRT vector: the rows of M that are even
+    under e -> -e relax at s_plus, the odd ones at s_minus, chosen from the "magic"
+    product (1/s_plus - 1/2)(1/s_minus - 1/2) = magic.  Every row of the three
+    bases is even or odd, so this is exactly the TRT operator."""
+    E = DIRECTIONS[lattice]
+    Q = len(E)
+    # parity of each row: rows whose moment changes sign under e -> -e (odd powers)
+    odd = {"D2Q9": [3, 4, 5, 6], "D3Q19": [3, 4, 5, 6, 7, 8, 16, 17, 18],
+           "D3Q15": [3, 4, 5, 6, 7, 8, 14]}[lattice]
+    s_minus = 1.0 / (magic / (1.0 / s_plus - 0.5) + 0.5)
+    s = np.full(Q, float(s_plus))
+    s[odd] = s_minus
+    return s
+
+
 def s_nu_for(nu_lattice):
     """Lattice viscosity nu = (1/s_nu - 1/2)/3 (Sec. 3 with eta h^2 = delta_t = 1)."""
     return 1.0 / (3.0 * nu_lattice + 0.5)

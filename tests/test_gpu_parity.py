@@ -246,3 +246,31 @@ def test_full_size_pipe_sampled_nodes():
         print("%s sampled full-size error %.3e" % (prec, err))
         assert err < tol
         del g
+
+
+@pytest.mark.parametrize("kind", ["bgk", "trt"])
+def test_other_collision_operators_through_the_same_sweep(kind):
+    """Remark (1) after Eq. 2.10: the boundary construction does not depend on the
+    collision.  BGK and TRT, written as MRT relaxation vectors, run through the same
+    sweep and boundary against the oracle (D2Q9 Couette with random walls, D3Q19
+    sphere box)."""
+    cases = []
+    w2 = W.couette_config(64)
+    w2["links"] = W.random_links_uw(w2["links"], 0.01, seed=8)
+    cases.append((w2, OL.D2Q9))
+    w3 = W.sphere_3d(12, 3.1, (5.7, 6.2, 5.4), s_nu=1.1, force=(1e-5, 0.0, 2e-6))
+    w3["links"] = W.random_links_uw(w3["links"], 0.01, seed=9)
+    cases.append((w3, OL.D3Q19))
+    for w, lat in cases:
+        w = dict(w)
+        w["S"] = (W.relaxation_rates_bgk(lat.name, 1.25) if kind == "bgk"
+                  else W.relaxation_rates_trt(lat.name, 1.25))
+        rho, u = W.random_state(w["shape"], lat.name, 1.0, 0.01, seed=10)
+        o = oracle_sim(w, scheme=(0, 1, 1, 0.9))
+        o.init_equilibrium(rho, u)
+        o.step(23)
+        g = gpu_sim(w, "f64", scheme=(0, 1, 1, 0.9))
+        g.init_equilibrium(rho, u)
+        g.step(23)
+        fl = ~w["solid"]
+        assert rel_err(deviation(g.get_populations(), lat), deviation(o.f, lat), fl) < TOL64

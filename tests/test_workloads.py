@@ -90,3 +90,18 @@ def test_ensemble_is_seeded():
     assert a == b
     assert all(48 <= p["n"] <= 768 for p in a)
     assert all(0.1 * p["n"] <= p["R1"] <= 0.25 * p["n"] for p in a)
+
+
+def test_trt_rows_follow_the_parity_of_m():
+    """The TRT vector puts s_minus exactly on the rows of M that are odd under
+    e -> -e (checked against the oracle's matrices) and satisfies the magic product."""
+    import numpy as np
+    from oracle import lattices as OL
+    for name in ("D2Q9", "D3Q19", "D3Q15"):
+        lat = OL.BY_NAME[name]
+        s = W.relaxation_rates_trt(name, 1.3, magic=0.25)
+        odd = np.array([np.allclose(lat.M[k][lat.opp], -lat.M[k]) for k in range(lat.Q)])
+        sm = s[odd]
+        assert np.allclose(sm, sm[0]) and np.allclose(s[~odd], 1.3)
+        assert abs((1 / 1.3 - 0.5) * (1 / sm[0] - 0.5) - 0.25) < 1e-14
+        assert np.all(W.relaxation_rates_bgk(name, 0.9) == 0.9)
