@@ -546,12 +546,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
       return (I)xc + (I)A.nx * ((I)yy + (I)A.ny * zz);
     };
     const int sy = SKEW ? A.sy : 0, sz = SKEW ? A.sz : 0;
+    // (a node can be on both edges when nx = 1)
     if (ODD && !ALIGNED && xlo) {          // aligned rows: staged with the windows
 #pragma unroll
       for (int i = 0; i < Q; ++i)
         if (L::ex(i) > 0)
           g[i] = Storage<T>::load(pop + (I)L::opp(i) * S + across(nxm1, sy - L::ey(i), sz - L::ez(i)));
-    } else if (ODD && !ALIGNED && xhi) {
+    }
+    if (ODD && !ALIGNED && xhi) {
 #pragma unroll
       for (int i = 0; i < Q; ++i)
         if (L::ex(i) < 0)
@@ -596,7 +598,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
           for (int i = 0; i < Q; ++i)
             if (L::ex(i) < 0)
               Storage<T>::store(pop + (I)i * S + across(nxm1, sy + L::ey(i), sz + L::ez(i)), gp[i]);
-        } else if (xhi) {
+        }
+        if (xhi) {
 #pragma unroll
           for (int i = 0; i < Q; ++i)
             if (L::ex(i) > 0)

@@ -274,3 +274,39 @@ def test_other_collision_operators_through_the_same_sweep(kind):
         g.step(23)
         fl = ~w["solid"]
         assert rel_err(deviation(g.get_populations(), lat), deviation(o.f, lat), fl) < TOL64
+
+
+@pytest.mark.parametrize("lattice,shape,skew,prec", [
+    ("D2Q9", (1, 9, 1), (0, 0), "f64"),     # one column: every node on both x-edges
+    ("D2Q9", (2, 7, 1), (0, 0), "f64"),
+    ("D2Q9", (3, 1, 1), (0, 0), "f64"),     # one row, no walls, no cut links
+    ("D3Q19", (1, 6, 5), (2, 1), "f64"),    # one column with a skewed x-wrap
+    ("D3Q19", (2, 5, 4), (0, 0), "f32"),
+    ("D3Q15", (1, 4, 4), (1, 3), "f64"),
+    ("D3Q19", (65, 4, 3), (0, 0), "f64"),   # a full tile plus a one-node tile per row
+])
+def test_thin_and_degenerate_grids(lattice, shape, skew, prec):
+    """Grids one or two nodes thick, a single row, and a ragged last tile: walls on the
+    first and last rows when there are at least four, random wall fractions and wall
+    velocities, random state, seven steps (both parities) against the oracle."""
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    y = (np.arange(N) // nx) % ny
+    solid = (y == 0) | (y == ny - 1) if ny >= 4 else np.zeros(N, bool)
+    node, d = W.cut_links(lattice, shape, skew, solid)
+    rng = np.random.default_rng(nx * 100 + ny * 10 + nz)
+    w = dict(lattice=lattice, shape=shape, skew=skew, solid=solid,
+             links=dict(node=node, d=d, q=rng.uniform(0.1, 1.0, len(node)),
+                        uw=0.01 * rng.standard_normal((len(node), 3))),
+             S=W.relaxation_rates(lattice, 1.2), rho0=1.0, force=(1e-5, -2e-6, 3e-6))
+    rho, u = W.random_state(shape, lattice, 1.0, 0.01, seed=3)
+    lat = OL.BY_NAME[lattice]
+    o = oracle_sim(w, scheme=(0, 1, 1, 0.9))
+    o.init_equilibrium(rho, u)
+    o.step(7)
+    g = gpu_sim(w, prec, scheme=(0, 1, 1, 0.9))
+    g.init_equilibrium(rho, u)
+    g.step(7)
+    fl = ~solid
+    err = rel_err(deviation(g.get_populations(), lat), deviation(o.f, lat), fl)
+    assert err < (TOL64 if prec == "f64" else 1e-5), err
