@@ -148,3 +148,29 @@ def test_batch_member_matches_oracle_and_d3q19_mix():
         fl = ~w["solid"]
         assert rel_err(deviation(s.get_populations(), OL.D3Q19), deviation(o.f, OL.D3Q19), fl) < 1e-12
     batch.close()
+
+
+def test_full_ensemble_batch_equals_one_launch_per_member():
+    """The benchmark's ensemble itself (96 Couette instances from seed 0, n in 48..768,
+    FP32): after tuning and an odd number of graph-replayed steps, every member of
+    the batch holds exactly what stepping it alone gives."""
+    torch = require_gpu()
+    stream = torch.cuda.current_stream().cuda_stream
+    ws = [W.ensemble_member(p) for p in W.couette_ensemble(96, 0)]
+    solo, grouped = [], []
+    for w in ws:
+        for lst in (solo, grouped):
+            s = gpu_sim(w, "f32")
+            s.init_equilibrium()
+            s.set_stream(stream)
+            lst.append(s)
+    batch = B.Batch(grouped)
+    batch.set_stream(stream)
+    batch.tune(4)
+    batch.step(7)
+    for s in solo:
+        s.step(7)
+    for a, b, w in zip(solo, grouped, ws):
+        fl = ~w["solid"]
+        assert np.array_equal(a.get_populations()[:, fl], b.get_populations()[:, fl])
+    batch.close()

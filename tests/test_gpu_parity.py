@@ -310,3 +310,56 @@ def test_thin_and_degenerate_grids(lattice, shape, skew, prec):
     fl = ~solid
     err = rel_err(deviation(g.get_populations(), lat), deviation(o.f, lat), fl)
     assert err < (TOL64 if prec == "f64" else 1e-5), err
+
+
+def test_full_size_couette_2048_sampled_nodes():
+    """The refinement study's largest grid (2048^2, D2Q9), FP64 and FP32: 3 steps from
+    a perturbed analytic start; 48 sampled nodes (both walls, interior) against the
+    oracle's patch evaluation."""
+    n = 2048
+    w = W.couette_config(n)
+    lat = OL.D2Q9
+    rng = np.random.default_rng(22)
+    N = n * n
+    rho = 1.0 + 0.001 * rng.standard_normal(N)
+    u = np.nan_to_num(w["u_exact"]) + 0.0005 * rng.standard_normal((N, 3))
+    u[:, 2] = 0.0
+    fl = np.nonzero(~w["solid"])[0]
+    bnd = np.unique(w["links"]["node"])
+    centres = np.concatenate([rng.choice(bnd, 32, replace=False), rng.choice(fl, 16, replace=False)])
+    k = 3
+    f0_fn = lambda idx: O.equilibrium(lat, rho[idx], u[idx].T, 1.0)
+    want = patch_reference(w, f0_fn, centres, k, (0, 1, 0, 1.0))
+    for prec, tol in (("f64", TOL64), ("f32", 1e-5)):
+        g = gpu_sim(w, prec)
+        g.init_equilibrium(rho, u[:, :2])
+        g.step(k)
+        err = rel_err(deviation(g.get_populations()[:, centres], lat), deviation(want, lat))
+        print("%s sampled 2048^2 error %.3e" % (prec, err))
+        assert err < tol
+        del g
+
+
+def test_full_size_d3q15_pipe_sampled_nodes():
+    """The bench's D3Q15 section size (L = 256 pipe), FP32, 2 steps, sampled nodes."""
+    L = 256
+    w = W.tilted_pipe_3d(L, lattice="D3Q15")
+    lat = OL.D3Q15
+    rng = np.random.default_rng(23)
+    N = L ** 3
+    rho = 1.0 + 0.001 * rng.standard_normal(N)
+    u = np.nan_to_num(w["u_exact"]) + 0.001 * rng.standard_normal((N, 3))
+    fl = np.nonzero(~w["solid"])[0]
+    bnd = np.unique(w["links"]["node"])
+    x = fl % L
+    edge = fl[(x == 0) | (x == L - 1)]
+    centres = np.concatenate([rng.choice(bnd, 16, replace=False), rng.choice(fl, 8, replace=False),
+                              rng.choice(edge, 8, replace=False)])
+    f0_fn = lambda idx: O.equilibrium(lat, rho[idx], u[idx].T, 1.0)
+    want = patch_reference(w, f0_fn, centres, 2, (0, 1, 0, 1.0))
+    g = gpu_sim(w, "f32")
+    g.init_equilibrium(rho, u)
+    g.step(2)
+    err = rel_err(deviation(g.get_populations()[:, centres], lat), deviation(want, lat))
+    print("D3Q15 f32 sampled full-size error %.3e" % err)
+    assert err < 1e-5
