@@ -149,6 +149,23 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(x, world, device):
+    """The slowest rank's value (timings are taken as the maximum over ranks)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(fluid_per_rank, steps, world, total_ms):
+    """Whole-job throughput of independent replicas (weak scaling): every rank
+    advances its own copy, the job takes as long as the slowest rank."""
+    return fluid_per_rank * steps * world / (total_ms * 1e-3) / 1e6
+
+
 def build_sim(w, precision, torch, stream):
     from paper_1712_08288_gb300 import binding as B
     sim = B.from_workload(w, precision, SCHEME)
@@ -207,12 +224,8 @@ def run_gpu(args):
     with ClockSampler(local) as clk:
         total_ms, launches = time_steps(sim, torch, stream, args.steps, args.warmup)
         barrier()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    mlups = n_fluid * args.steps * world / (total_ms * 1e-3) / 1e6
+    total_ms = max_over_ranks(total_ms, world, "cuda")
+    mlups = job_mlups(n_fluid, args.steps, world, total_ms)
     launch_ms = float(np.mean(launches))
     hbm, peak_kind = peaks()
     alg_bytes = 2 * Q * BYTES["f32"] * n_fluid          # populations read + written
