@@ -114,7 +114,7 @@ int lbm_set_skew(lbm_ctx *ctx, int sy, int sz);
  *   q[k]     wall fraction gamma in (0, 1]: the wall point is x_b = x_f + q e_d
  *            (the paper's x_b = x_f - gamma h e_i).
  *   uw       NULL (walls at rest) or 3*n_links wall velocities phi(x_b) (third
- *            component ignored in 2D), held fixed in time.
+ *            component ignored in 2D), scaled per step by lbm_set_wall_factor.
  * Every fluid->solid pair must be listed exactly once; anything else is
  * LBM_EINVAL.  If the current scheme makes a link non-convex (Eq. 2.12) and
  * non-convex schemes were not allowed, LBM_ENONCONVEX.  Resets the populations
