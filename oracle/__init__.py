@@ -11,11 +11,13 @@ Layout
 ``lattices``  velocity sets, weights, MRT matrices (Appendix; D3Q19 from the
               d'Humieres et al. 2002 polynomial basis the Appendix cites).
 ``adjoint``   reverse-mode (discrete adjoint) of ``lbm`` for a velocity-mismatch
-              loss; gradients with respect to S, per-link q and wall velocity.
+              loss; gradients with respect to S, per-link q and wall velocity
+              (single-node scheme).
 ``lbm``       one lattice-Boltzmann step: MRT collision (Appendix), equilibrium
               Eq. (42), advection Eq. (2.2b), the boundary scheme Eq. (2.13) built
-              from Eqs. (2.5)-(2.7) and (2.9) in the paper's order, moments and the
-              relative L2 error of Sec. 3.1.
+              from Eqs. (2.5)-(2.7) and (2.9) in the paper's order (optionally the
+              two-node variant of Remark (2), Eq. 2.11), moments and the relative L2
+              error of Sec. 3.1.
 
 Everything is float64 numpy; dense matrices, two population arrays (pre- and
 post-collision), push streaming.  No blocking, fusion or reordering beyond what the
