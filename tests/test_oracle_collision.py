@@ -15,6 +15,26 @@ def _random_f(lat, n, seed, scale=0.05):
     return lat.w[:, None] * (1.0 + scale * rng.standard_normal((lat.Q, n)))
 
 
+def test_d3q15_equilibrium_moments_dhumieres():
+    """M f^eq for the Appendix's D3Q15 equals the D3Q15 equilibrium moments of
+    d'Humieres et al. (2002) in incompressible form (j/rho0): e = -rho + j^2/rho0,
+    eps = rho - 5 j^2/rho0, q = -7/3 j, 3p_xx = (3jx^2 - j^2)/rho0,
+    p_ww = (jy^2 - jz^2)/rho0, p_ab = ja jb/rho0, m_xyz = 0."""
+    rng = np.random.default_rng(4)
+    n = 40
+    rho = 1 + 0.1 * rng.standard_normal(n)
+    u = 0.05 * rng.standard_normal((3, n))
+    jx, jy, jz = RHO0 * u
+    j2 = jx * jx + jy * jy + jz * jz
+    z = np.zeros(n)
+    want = np.array([rho, -rho + j2 / RHO0, rho - 5 * j2 / RHO0,
+                     jx, -7 / 3 * jx, jy, -7 / 3 * jy, jz, -7 / 3 * jz,
+                     (3 * jx * jx - j2) / RHO0, (jy * jy - jz * jz) / RHO0,
+                     jx * jy / RHO0, jy * jz / RHO0, jx * jz / RHO0, z])
+    got = L.D3Q15.M @ O.equilibrium(L.D3Q15, rho, u, RHO0)
+    assert np.abs(got - want).max() < 1e-14
+
+
 @pytest.mark.parametrize("lat", [L.D2Q9, L.D3Q15, L.D3Q19])
 def test_equilibrium_moments_closed_form(lat):
     """Incompressible equilibrium (He & Luo 1997; Eq. (42)): sum f^eq = rho,
