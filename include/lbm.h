@@ -86,7 +86,8 @@ enum lbm_status {
 
 /* Create a context on the current CUDA device.
  *   lattice   LBM_D2Q9, LBM_D3Q19 or LBM_D3Q15; nz must be 1 for D2Q9.
- *   nx,ny,nz  grid size, each >= 1 (>= 3 along any axis a fluid link crosses).
+ *   nx,ny,nz  grid size, each >= 1 (one- and two-node extents are periodic like
+ *             any other: a node may be its own neighbour across the wrap).
  *   s         Q relaxation rates in the moment order above (diagonal of S,
  *             Appendix); the rates of rho and j have no effect (conserved).
  *   precision an lbm_precision.
