@@ -24,3 +24,23 @@ def test_library_exports_every_declared_symbol():
     lib = binding.load_library(path)
     missing = [n for n in declared_functions() if not hasattr(lib, n)]
     assert not missing, missing
+
+
+def test_product_path_does_not_touch_the_oracle_and_fails_loudly_without_the_library():
+    """The package and its binding never import the oracle, and a missing library
+    is an ImportError, not a fallback."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "import paper_1712_08288_gb300, paper_1712_08288_gb300.binding as B, "
+        "paper_1712_08288_gb300.workloads\n"
+        "assert not any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules), 'oracle imported'\n"
+        "try:\n"
+        "    B.load_library('/nonexistent/liblbm.so')\n"
+        "    raise SystemExit('no error')\n"
+        "except ImportError:\n"
+        "    pass\n" % root)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
