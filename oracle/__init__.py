@@ -26,7 +26,7 @@ equations state.
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 (``tests/test_oracle_*.py``) against printed tables, closed forms, textbook special
 cases or invariants.  The only quantitative results the paper prints are the
-matrices M and the statement that observed orders are "around 2"; its convergence
+matrices M and the statement that the observed orders are close to 2; its convergence
 plots are not available, so the oracle's absolute error values are not pinned to the
 paper (only their order of convergence is).
 """

@@ -1,6 +1,6 @@
 """Pins of the whole oracle against analytic flows and the paper's observed orders.
 
-Sec. 3.1 of arXiv:1712.08288 reports convergence orders "around 2" for the five
+Sec. 3.1 of arXiv:1712.08288 reports convergence orders near 2 for the five
 l-rules on the Poiseuille channel (its plots are not available, only this statement);
 Sec. 3.3 reports second order for the pipe.  The circular Couette flow is the
 textbook steady solution u_theta = U1 R1 (R2^2/r - r)/(R2^2 - R1^2).
