@@ -236,7 +236,8 @@ int lbm_set_link_values(lbm_ctx *ctx, const double *q, const double *uw);
  *   grad_uw   3*n_links doubles: dJ/dphi per link, or NULL.
  * The adjoint computes in double for LBM_F64 and in float otherwise; gradients
  * are accumulated in double.  Memory: about (n_steps/checkpoint_every +
- * checkpoint_every + 3) population arrays. */
+ * checkpoint_every + 3) population arrays, kept in the context after a successful
+ * call and reused (grown when needed) by later calls; lbm_destroy releases it. */
 int lbm_adjoint(lbm_ctx *ctx, int n_steps, int checkpoint_every, const uint8_t *mask,
                 const double *u_target, double *loss, double *grad_s, double *grad_q,
                 double *grad_uw);

@@ -92,6 +92,8 @@ struct lbm_ctx {
   std::vector<double> link_q;
   std::vector<double> link_uw;  // 3 per link
   std::vector<int64_t> link_src; // input position of the link at each device position
+  // device workspace of lbm_adjoint (pointer, capacity), kept between calls
+  std::pair<void *, size_t> adj_ws[13] = {};
   long long n_links = 0, n_fluid = 0, n_boundary = 0;
 
   SweepArgs<double> a64;
@@ -261,6 +263,29 @@ static int upload_coefficients(lbm_ctx *c) {
   return LBM_OK;
 }
 
+// buffer `slot` of the adjoint's workspace with at least `bytes`, grown when needed
+static cudaError_t adj_ws_get(lbm_ctx *c, int slot, size_t bytes, void **p) {
+  auto &e = c->adj_ws[slot];
+  if (e.second < bytes) {
+    cudaFree(e.first);
+    e = {nullptr, 0};
+    const cudaError_t r = cudaMalloc(&e.first, bytes);
+    if (r != cudaSuccess) {
+      e.first = nullptr;
+      return r;
+    }
+    e.second = bytes;
+  }
+  *p = e.first;
+  return cudaSuccess;
+}
+static void adj_ws_free(lbm_ctx *c) {
+  for (auto &e : c->adj_ws) {
+    cudaFree(e.first);
+    e = {nullptr, 0};
+  }
+}
+
 static void free_two_node(lbm_ctx *c) {
   cudaFree(c->tn); c->tn = nullptr;
   cudaFree(c->tn_delta); c->tn_delta = nullptr;
@@ -427,6 +452,7 @@ int lbm_destroy(lbm_ctx *c) {
   cudaFree(c->cls);
   cudaFree(c->status);
   free_geometry(c);
+  adj_ws_free(c);
   cudaFree(c->tiles);
   c->tiles = nullptr;
   cudaFree(c->rec32);
@@ -879,10 +905,10 @@ int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *ma
   const long long pblocks = adjoint_partial_blocks(c->N);
   std::vector<long long> tck(nseg);
   int rc = LBM_OK;
+  // on failure the workspace is released; on success it stays for the next call
+  bool ok = false;
   auto cleanup = [&]() {
-    cudaFree(ck); cudaFree(seg); cudaFree(fin); cudaFree(lam0); cudaFree(lam1); cudaFree(dmask);
-    cudaFree(dut); cudaFree(dgs); cudaFree(dtot); cudaFree(dJ); cudaFree(gpart);
-    cudaFree(dcoef); cudaFree(acc);
+    if (!ok) adj_ws_free(c);
     c->a64.save = nullptr;
     c->a32.save = nullptr;
   };
@@ -895,21 +921,21 @@ int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *ma
                   cudaGetErrorString(e_));                                                  \
     }                                                                                       \
   } while (0)
-  ADJ_CUDA(cudaMalloc((void **)&ck, (c->precision == LBM_F64 || c->precision == LBM_F32_DEV
-                                        ? state : raw_pop + raw_lnk) * nseg));
-  ADJ_CUDA(cudaMalloc((void **)&seg, state * K));
-  ADJ_CUDA(cudaMalloc((void **)&fin, raw_pop + raw_lnk));
-  ADJ_CUDA(cudaMalloc((void **)&lam0, state));
-  ADJ_CUDA(cudaMalloc((void **)&lam1, state));
-  ADJ_CUDA(cudaMalloc((void **)&dmask, c->N));
-  ADJ_CUDA(cudaMalloc((void **)&dut, sizeof(double) * c->N * c->D));
-  ADJ_CUDA(cudaMalloc((void **)&dgs, sizeof(double) * 19));
   const long long nl1 = std::max<long long>(1, nl);
-  ADJ_CUDA(cudaMalloc((void **)&dtot, sizeof(double) * 2 * nl1));
-  ADJ_CUDA(cudaMalloc(&acc, csize * 2 * nl1));
-  ADJ_CUDA(cudaMalloc(&dcoef, csize * 4 * nl1));
-  ADJ_CUDA(cudaMalloc((void **)&dJ, sizeof(double)));
-  ADJ_CUDA(cudaMalloc((void **)&gpart, sizeof(double) * c->Q * pblocks));
+  ADJ_CUDA(adj_ws_get(c, 0, (c->precision == LBM_F64 || c->precision == LBM_F32_DEV
+                                 ? state : raw_pop + raw_lnk) * nseg, (void **)&ck));
+  ADJ_CUDA(adj_ws_get(c, 1, state * K, (void **)&seg));
+  ADJ_CUDA(adj_ws_get(c, 2, raw_pop + raw_lnk, (void **)&fin));
+  ADJ_CUDA(adj_ws_get(c, 3, state, (void **)&lam0));
+  ADJ_CUDA(adj_ws_get(c, 4, state, (void **)&lam1));
+  ADJ_CUDA(adj_ws_get(c, 5, c->N, (void **)&dmask));
+  ADJ_CUDA(adj_ws_get(c, 6, sizeof(double) * c->N * c->D, (void **)&dut));
+  ADJ_CUDA(adj_ws_get(c, 7, sizeof(double) * 19, (void **)&dgs));
+  ADJ_CUDA(adj_ws_get(c, 8, sizeof(double) * 2 * nl1, (void **)&dtot));
+  ADJ_CUDA(adj_ws_get(c, 9, csize * 2 * nl1, &acc));
+  ADJ_CUDA(adj_ws_get(c, 10, csize * 4 * nl1, &dcoef));
+  ADJ_CUDA(adj_ws_get(c, 11, sizeof(double), (void **)&dJ));
+  ADJ_CUDA(adj_ws_get(c, 12, sizeof(double) * c->Q * pblocks, (void **)&gpart));
   cudaStream_t st = c->stream;
   ADJ_CUDA(cudaMemsetAsync(gpart, 0, sizeof(double) * c->Q * pblocks, st));
   ADJ_CUDA(cudaMemsetAsync(lam1, 0, state, st));        // solid entries stay zero
@@ -1024,6 +1050,7 @@ int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *ma
   if (nl)
     ADJ_CUDA(cudaMemcpyAsync(htot.data(), dtot, sizeof(double) * 2 * nl, cudaMemcpyDeviceToHost, st));
   ADJ_CUDA(cudaStreamSynchronize(st));
+  ok = true;
   cleanup();
 #undef ADJ_CUDA
   if (loss) *loss = hJ;
