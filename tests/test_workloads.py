@@ -105,3 +105,29 @@ def test_trt_rows_follow_the_parity_of_m():
         assert np.allclose(sm, sm[0]) and np.allclose(s[~odd], 1.3)
         assert abs((1 / 1.3 - 0.5) * (1 / sm[0] - 0.5) - 0.25) < 1e-14
         assert np.all(W.relaxation_rates_bgk(name, 0.9) == 0.9)
+
+
+def test_taylor_green_disc_generator():
+    """Sec. 3.2 inputs: every cut link's wall point lies on the circle of radius 1/4
+    about (1/2, 1/2), q in (0, 1], nodes on the rim are solid, the wall velocity is
+    the analytic field at the wall point (in lattice units), and T = 1/U0 in steps."""
+    import numpy as np
+    inv_h, s_nu = 40, 1.0
+    w = W.taylor_green_disc(inv_h, s_nu)
+    h = 1.0 / inv_h
+    n = inv_h + 1
+    node, d, q, uw = (w["links"][k] for k in ("node", "d", "q", "uw"))
+    E = W.DIRECTIONS["D2Q9"]
+    x, y = (node % n) * h, (node // n) * h
+    xb, yb = x + q * E[d, 0] * h, y + q * E[d, 1] * h
+    assert np.allclose(np.hypot(xb - 0.5, yb - 0.5), 0.25, atol=1e-12, rtol=0)
+    assert np.all((q > 0) & (q <= 1))
+    X, Y = (np.arange(n * n) % n) * h, (np.arange(n * n) // n) * h
+    on_rim = np.isclose(np.hypot(X - 0.5, Y - 0.5), 0.25, atol=1e-12)
+    assert on_rim.any() and np.all(w["solid"][on_rim])
+    eta = (1 / s_nu - 0.5) / (3 * 0.002)
+    u_b = -0.05 * np.cos(2 * np.pi * xb) * np.sin(2 * np.pi * yb) * eta * h
+    v_b = 0.05 * np.cos(2 * np.pi * yb) * np.sin(2 * np.pi * xb) * eta * h
+    assert np.allclose(uw[:, 0], u_b, atol=1e-15) and np.allclose(uw[:, 1], v_b, atol=1e-15)
+    assert abs(w["steps"] * eta * h * h - 1 / 0.05) < eta * h * h
+    assert abs(w["decay"] - np.exp(-8 * np.pi ** 2 * 0.002 * eta * h * h)) < 1e-15
