@@ -131,3 +131,18 @@ def test_two_node_scheme_is_second_order(rule, gamma):
     errs = [poiseuille_error(n, gamma, 1.0, rule, two_node=True) for n in sizes]
     inv_h = [n - 2 + 2 * gamma for n in sizes]
     assert 1.85 < observed_order(inv_h, errs) < 2.4, errs
+
+
+def test_hagen_poiseuille_order_d3q15():
+    """The paper's own 3D setup (Sec. 3.3, D3Q15 with the Appendix's M and the S of
+    Sec. 3, pipe along x): the error falls by ~4 from L = 12 to L = 24."""
+    errs = []
+    for Lb in (12, 24):
+        w = W.tilted_pipe_3d(Lb, axis_dir=(1, 0, 0), lattice="D3Q15")
+        sim = O.Simulation(L.D3Q15, w["shape"], w["S"], w["rho0"], w["solid"], w["links"],
+                           scheme=(0, 1, 0, 1.0), force=w["force"], skew=w["skew"])
+        sim.init_equilibrium(None, np.nan_to_num(w["u_exact"]))
+        run_to_steady(sim, 1e-9, chunk=100)
+        _, u = sim.moments()
+        errs.append(O.relative_l2_error(w["u_exact"], u, ~w["solid"]))
+    assert 1.8 < np.log2(errs[0] / errs[1]) < 2.4, errs
