@@ -27,13 +27,20 @@ def _case_3d():
     return L.D3Q19, w, S, (1e-5, 0.0, 2e-5)
 
 
+def _case_3d_q15():
+    w = W.sphere_3d(6, 1.7, (2.6, 3.1, 2.4), s_nu=1.1, lattice="D3Q15")
+    w["links"] = W.random_links_uw(w["links"], 0.01, seed=5)
+    S = W.relaxation_rates("D3Q15", 1.1)
+    return L.D3Q15, w, S, (1e-5, 2e-5, 0.0)
+
+
 def _run(lat, w, S, g, scheme, links, steps, mask, ut, rho, u, grad):
     sim = O.Simulation(lat, w["shape"], S, 1.0, w["solid"], links, scheme=scheme, force=g)
     sim.init_equilibrium(rho, u)
     return A.adjoint(sim, steps, mask, ut) if grad else A.loss(sim, steps, mask, ut)
 
 
-@pytest.mark.parametrize("case", [_case_2d, _case_3d])
+@pytest.mark.parametrize("case", [_case_2d, _case_3d, _case_3d_q15])
 @pytest.mark.parametrize("scheme", [(0, 1, 0, 1.0), (0, 1, 1, 0.7)])
 def test_adjoint_matches_finite_differences(case, scheme):
     lat, w, S, g = case()
