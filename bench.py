@@ -13,6 +13,15 @@ and the accuracy of both against the analytic Hagen-Poiseuille profile is report
 after an untimed run.  The populations (1.27 GB in FP32) exceed L2 (129 MB), so
 no flush is needed between steps.
 
+Untimed-for-the-headline sections of the same JSON line (rank 0; each can be turned
+off with its flag): "d3q15" (the same pipe with the paper's D3Q15), "accuracy"
+(E_r of FP32 and FP64 after 20000 steps at L = 128), "ensemble" (96 uneven Couette
+instances, one batched graph launch per step against one launch per instance),
+"refinement" (curved-wall Couette to steady state, n = 32..512, order; D2Q9
+throughput at n = 2048), "taylor_green" (the moving-wall disc of Sec. 3.2, order),
+"adjoint" (128^3 sphere, 2000 steps, backward/forward time and central-difference
+check), "e2e" (the headline through the C-ABI with host buffers), "cpu_baseline".
+
 --impl reference times the FP64 CPU oracle (the only reference implementation of
 this method: the paper ships no code) on the host cores, on a bounded sample of
 the same workload family.
