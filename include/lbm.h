@@ -242,7 +242,7 @@ int lbm_adjoint(lbm_ctx *ctx, int n_steps, int checkpoint_every, const uint8_t *
                 const double *u_target, double *loss, double *grad_s, double *grad_q,
                 double *grad_uw);
 
-/* Batches (ensembles of independent problems)./* Batches (ensembles of independent problems).  A batch advances several contexts
+/* Batches (ensembles of independent problems).  A batch advances several contexts
  * -- same lattice, precision and device, any sizes, geometries and parameters --
  * by ONE persistent sweep launch per time step that walks the tiles of all of them,
  * replayed from a CUDA graph holding an even and an odd step.  Each context keeps

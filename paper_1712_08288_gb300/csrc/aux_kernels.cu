@@ -43,7 +43,6 @@ __global__ void init_eq_kernel(AuxArgs a, const double *rho, const double *u) {
 
 template <class L, class T>
 __global__ void get_pop_kernel(AuxArgs a, bool odd, double *f) {
-  const T *pop = static_cast<const T *>(a.pop);
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < a.N;
        n += (long long)gridDim.x * blockDim.x) {
     const bool solid = a.cls[n] == kSolid;
