@@ -42,6 +42,47 @@ def rel_err(a, b, mask=None):
     return float(np.sqrt(((a - b) ** 2).sum()) / np.sqrt((b ** 2).sum()))
 
 
+def entry_err(a, b, mask=None):
+    """max_k |a_k - b_k| / max_k |b_k| over the masked entries: the bound on every
+    single entry, relative to the largest entry of the reference."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    if mask is not None:
+        a, b = a[..., mask], b[..., mask]
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def check_close(a, b, tol, mask=None, label=""):
+    """Element-wise parity: every compared entry satisfies |a_k - b_k| <= tol max|b|
+    (the per-entry bound), and the whole set ||a - b||_2 <= tol ||b||_2.  Non-finite
+    entries fail.  Prints both figures and the worst entry; returns (entry, norm)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    if mask is not None:
+        a, b = a[..., mask], b[..., mask]
+    assert a.shape == b.shape, (a.shape, b.shape)
+    assert np.isfinite(a).all(), "%s: non-finite entries" % label
+    d = np.abs(a - b)
+    scale = np.abs(b).max()
+    entry = float(d.max() / scale)
+    norm = float(np.sqrt((d ** 2).sum()) / np.sqrt((b ** 2).sum()))
+    worst = np.unravel_index(int(np.argmax(d)), d.shape)
+    print("parity %s: per-entry %.3e, norm %.3e (tol %.1e; worst entry %s: %.17g vs %.17g)"
+          % (label, entry, norm, tol, tuple(int(v) for v in worst), a[worst], b[worst]))
+    assert entry <= tol, "%s: per-entry error %.3e > %.1e at %s" % (label, entry, tol, worst)
+    assert norm <= tol, "%s: norm error %.3e > %.1e" % (label, norm, tol)
+    return entry, norm
+
+
+def check_fd(fd, g, rtol, floor, label=""):
+    """A gradient entry against its central difference: |fd - g| <= rtol |fd| + floor,
+    floor the difference quotient's own rounding (stated by the caller)."""
+    err = abs(fd - g)
+    print("fd %s: fd %.10e adjoint %.10e rel %.3e (floor %.1e)"
+          % (label, fd, g, err / abs(fd) if fd else float("inf"), floor))
+    assert err <= rtol * abs(fd) + floor, (label, fd, g)
+
+
 def deviation(f, lat):
     """Population deviations g = f - w rho0 (rho0 = 1)."""
     return f - lat.w[:, None]

@@ -9,7 +9,7 @@ from oracle import lattices as OL
 from paper_1712_08288_gb300 import binding as B
 from paper_1712_08288_gb300 import workloads as W
 
-from gpu_common import deviation, gpu_sim, oracle_sim, rel_err, require_gpu
+from gpu_common import check_close, deviation, gpu_sim, oracle_sim, require_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -146,7 +146,7 @@ def test_batch_member_matches_oracle_and_d3q19_mix():
         o.init_equilibrium(rho, u)
         o.step(9)
         fl = ~w["solid"]
-        assert rel_err(deviation(s.get_populations(), OL.D3Q19), deviation(o.f, OL.D3Q19), fl) < 1e-12
+        check_close(deviation(s.get_populations(), OL.D3Q19), deviation(o.f, OL.D3Q19), 1e-12, fl)
     batch.close()
 
 

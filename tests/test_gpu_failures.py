@@ -14,7 +14,7 @@ from gpu_common import gpu_sim, require_gpu
 
 pytestmark = pytest.mark.gpu
 
-EINVAL, ENONCONVEX, EDIVERGED = -1, -4, -5
+EINVAL, ENONCONVEX, EDIVERGED, ETIMEOUT = -1, -4, -5, -6
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -85,3 +85,32 @@ def test_invalid_inputs_are_rejected_before_any_launch():
     assert _code(lambda: g.step(-1)) == EINVAL
     g.step(0)                                                        # nothing to do
     assert g.time() == 0
+
+
+@pytest.mark.parametrize("lattice,prec", [("D2Q9", "f32"), ("D3Q19", "f64"), ("D3Q19", "bf16")])
+def test_bounded_wait_gives_up_and_reports_timeout(lattice, prec):
+    """The sweep's bounded wait, made to run out on the host's say: with a wait
+    limit of zero polls every warp gives up at its first tile (after waiting, with
+    the default limit, for its own copies in flight), the step leaves the
+    populations untouched and the next read-out reports LBM_ETIMEOUT.  With the
+    default limit back and a new initial state the context steps like a fresh one."""
+    w = W.couette_config(48) if lattice == "D2Q9" else W.tilted_pipe_3d(32)
+    u0 = np.nan_to_num(w["u_exact"])
+    g = gpu_sim(w, prec)
+    g.init_equilibrium(None, u0)
+    f0 = g.get_populations()
+    g.set_wait_limit(0)
+    g.step(2)                      # an even count: the layout parity is unchanged
+    assert _code(lambda: g.moments()) == ETIMEOUT
+    assert _code(lambda: g.error_norms()) == ETIMEOUT
+    fl = ~w["solid"]
+    assert np.array_equal(g.get_populations()[:, fl], f0[:, fl])   # no tile was processed
+    assert _code(lambda: g.set_wait_limit(-1)) == EINVAL
+    g.set_wait_limit(1000)
+    g.init_equilibrium(None, u0)
+    g.step(6)
+    ref = gpu_sim(w, prec)
+    ref.init_equilibrium(None, u0)
+    ref.step(6)
+    assert g.error_norms()["status"] == 0
+    assert np.array_equal(g.get_populations()[:, fl], ref.get_populations()[:, fl])

@@ -10,7 +10,7 @@ import pytest
 
 from paper_1712_08288_gb300 import workloads as W
 
-from gpu_common import gpu_sim, require_gpu
+from gpu_common import check_fd, gpu_sim, require_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -103,7 +103,7 @@ def test_taylor_green_moving_wall_matches_oracle():
     lbm_set_wall_factor) against the oracle with phi(x_b, t) reset before each step."""
     from oracle import lattices as OL
     from oracle import lbm as O
-    from gpu_common import deviation, rel_err
+    from gpu_common import check_close, deviation
     w = W.taylor_green_disc(40, 1.0)
     o = O.Simulation(OL.D2Q9, w["shape"], w["S"], 1.0, w["solid"], w["links"],
                      scheme=RULES["g2+g"] + (1.0,))
@@ -116,7 +116,7 @@ def test_taylor_green_moving_wall_matches_oracle():
     g = _tg_gpu(w, "g2+g")
     g.step(steps)
     fl = ~w["solid"]
-    assert rel_err(deviation(g.get_populations(), OL.D2Q9), deviation(o.f, OL.D2Q9), fl) < 1e-12
+    check_close(deviation(g.get_populations(), OL.D2Q9), deviation(o.f, OL.D2Q9), 1e-12, fl)
 
 
 @pytest.mark.parametrize("s_nu", [0.5, 1.0, 1.5, 1.99])
@@ -160,17 +160,17 @@ def test_adjoint_follows_the_wall_factor():
     J, gs, gq, gp = run()
     q0 = w["links"]["q"].copy()
     uw0 = w["links"]["uw"].copy()
-    scale = max(np.abs(gq).max(), np.abs(gp).max())
     h = 1e-6
+    floor = 1e-12 * abs(J) / h      # rounding of two FP64 evaluations of J over 2h
     for k in rng.choice(len(q0), 3, replace=False):
         qp, qm = q0.copy(), q0.copy()
         qp[k] = min(q0[k] + h, 1.0)
         qm[k] = q0[k] - h
         fd = (run(q=qp)[0] - run(q=qm)[0]) / (qp[k] - qm[k])
-        assert abs(fd - gq[k]) <= 1e-5 * scale
+        check_fd(fd, gq[k], 1e-5, floor, "TG dJ/dq[%d]" % k)
         for a in range(2):
             up, um = uw0.copy(), uw0.copy()
             up[k, a] += h
             um[k, a] -= h
             fd = (run(uw=up)[0] - run(uw=um)[0]) / (2 * h)
-            assert abs(fd - gp[k, a]) <= 1e-5 * scale
+            check_fd(fd, gp[k, a], 1e-5, floor, "TG dJ/dphi[%d,%d]" % (k, a))

@@ -21,13 +21,16 @@ from oracle import lattices as OL
 from oracle import lbm as O
 from paper_1712_08288_gb300 import workloads as W
 
-from gpu_common import deviation, gpu_sim, oracle_sim, patch_reference, rel_err, require_gpu
+from gpu_common import check_close, deviation, gpu_sim, oracle_sim, patch_reference, require_gpu
 
 pytestmark = pytest.mark.gpu
 
 RULES = [(0, 1, 0), (0, 1.5, 0), (0, 2, 0), (0, 0, 1), (0, 1, 1)]
 TOL64 = 1e-12
 TOL_U = {"f32": 2e-6, "bf16": 5e-2, "f16": 1e-2}
+# FP32 deviations over a few steps: a step rounds each deviation a few times at
+# 2^-24 relative to the largest deviation in play
+TOL32_STEPS = 1e-6
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -65,11 +68,11 @@ def test_couette_64_f64_3000_steps():
     g.step(3000)
     fl = ~w["solid"]
     _, ug = g.moments()
-    assert rel_err(ug[fl], _u_oracle(o)[fl]) < TOL64
+    check_close(ug[fl], _u_oracle(o)[fl], TOL64, None)
     fg = g.get_populations()
-    assert rel_err(fg, o.f, fl) < TOL64
+    check_close(fg, o.f, TOL64, fl)
     # the deviations agree to the oracle's own accumulated rounding (see module doc)
-    assert rel_err(deviation(fg, OL.D2Q9), deviation(o.f, OL.D2Q9), fl) < 1e-10
+    check_close(deviation(fg, OL.D2Q9), deviation(o.f, OL.D2Q9), 1e-10, fl)
 
 
 @pytest.mark.parametrize("rule", RULES)
@@ -90,9 +93,9 @@ def test_d2q9_family_random_walls(rule, b):
     g.init_equilibrium(rho, u)
     g.step(41)
     fl = ~w["solid"]
-    assert rel_err(deviation(g.get_populations(), OL.D2Q9), deviation(o.f, OL.D2Q9), fl) < TOL64
+    check_close(deviation(g.get_populations(), OL.D2Q9), deviation(o.f, OL.D2Q9), TOL64, fl)
     _, ug = g.moments()
-    assert rel_err(ug[fl], _u_oracle(o)[fl]) < TOL64
+    check_close(ug[fl], _u_oracle(o)[fl], TOL64, None)
 
 
 @pytest.mark.parametrize("steps", [1, 2, 17])
@@ -119,7 +122,7 @@ def test_d3q19_sphere_ragged_box(steps):
     g.init_equilibrium(rho, u)
     g.step(steps)
     fl = ~w["solid"]
-    assert rel_err(deviation(g.get_populations(), OL.D3Q19), deviation(o.f, OL.D3Q19), fl) < TOL64
+    check_close(deviation(g.get_populations(), OL.D3Q19), deviation(o.f, OL.D3Q19), TOL64, fl)
 
 
 def test_d3q19_tilted_pipe_skewed_wrap():
@@ -135,7 +138,7 @@ def test_d3q19_tilted_pipe_skewed_wrap():
     g.init_equilibrium(rho, u)
     g.step(60)
     fl = ~w["solid"]
-    assert rel_err(deviation(g.get_populations(), OL.D3Q19), deviation(o.f, OL.D3Q19), fl) < TOL64
+    check_close(deviation(g.get_populations(), OL.D3Q19), deviation(o.f, OL.D3Q19), TOL64, fl)
 
 
 @pytest.mark.parametrize("prec", ["f32", "bf16", "f16"])
@@ -152,9 +155,7 @@ def test_reduced_precision_bounds_couette(prec):
     g.step(3000)
     fl = ~w["solid"]
     _, ug = g.moments()
-    err = rel_err(ug[fl], _u_oracle(o)[fl])
-    print("%s velocity error vs FP64 oracle: %.3e" % (prec, err))
-    assert err < TOL_U[prec]
+    check_close(ug[fl], _u_oracle(o)[fl], TOL_U[prec], None, "%s couette u" % prec)
 
 
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
@@ -169,9 +170,7 @@ def test_reduced_precision_d3q19_pipe(prec):
     g.step(200)
     fl = ~w["solid"]
     _, ug = g.moments()
-    err = rel_err(ug[fl], _u_oracle(o)[fl])
-    print("%s pipe velocity error vs FP64 oracle: %.3e" % (prec, err))
-    assert err < TOL_U[prec]
+    check_close(ug[fl], _u_oracle(o)[fl], TOL_U[prec], None, "%s pipe u" % prec)
 
 
 def test_populations_round_trip_and_parity_layouts():
@@ -192,7 +191,7 @@ def test_populations_round_trip_and_parity_layouts():
     o.f = ff
     o.step(3)
     g.step(3)
-    assert rel_err(deviation(g.get_populations(), OL.D3Q19), deviation(o.f, OL.D3Q19), fl) < TOL64
+    check_close(deviation(g.get_populations(), OL.D3Q19), deviation(o.f, OL.D3Q19), TOL64, fl)
 
 
 def test_error_norms_match_host_formula():
@@ -237,14 +236,12 @@ def test_full_size_pipe_sampled_nodes():
     k = 2
     f0_fn = lambda idx: O.equilibrium(lat, rho[idx], u[idx].T, 1.0)
     want = patch_reference(w, f0_fn, centres, k, (0, 1, 0, 1.0))
-    for prec, tol in (("f64", TOL64), ("f32", 1e-5)):
+    for prec, tol in (("f64", TOL64), ("f32", TOL32_STEPS)):
         g = gpu_sim(w, prec)
         g.init_equilibrium(rho, u)
         g.step(k)
         f = g.get_populations()[:, centres]
-        err = rel_err(deviation(f, lat), deviation(want, lat))
-        print("%s sampled full-size error %.3e" % (prec, err))
-        assert err < tol
+        check_close(deviation(f, lat), deviation(want, lat), tol, None, "%s L=256 samples" % prec)
         del g
 
 
@@ -273,7 +270,7 @@ def test_other_collision_operators_through_the_same_sweep(kind):
         g.init_equilibrium(rho, u)
         g.step(23)
         fl = ~w["solid"]
-        assert rel_err(deviation(g.get_populations(), lat), deviation(o.f, lat), fl) < TOL64
+        check_close(deviation(g.get_populations(), lat), deviation(o.f, lat), TOL64, fl)
 
 
 @pytest.mark.parametrize("lattice,shape,skew,prec", [
@@ -308,8 +305,8 @@ def test_thin_and_degenerate_grids(lattice, shape, skew, prec):
     g.init_equilibrium(rho, u)
     g.step(7)
     fl = ~solid
-    err = rel_err(deviation(g.get_populations(), lat), deviation(o.f, lat), fl)
-    assert err < (TOL64 if prec == "f64" else 1e-5), err
+    check_close(deviation(g.get_populations(), lat), deviation(o.f, lat),
+                TOL64 if prec == "f64" else TOL32_STEPS, fl, "%s %s %s" % (lattice, shape, prec))
 
 
 def test_full_size_couette_2048_sampled_nodes():
@@ -330,13 +327,12 @@ def test_full_size_couette_2048_sampled_nodes():
     k = 3
     f0_fn = lambda idx: O.equilibrium(lat, rho[idx], u[idx].T, 1.0)
     want = patch_reference(w, f0_fn, centres, k, (0, 1, 0, 1.0))
-    for prec, tol in (("f64", TOL64), ("f32", 1e-5)):
+    for prec, tol in (("f64", TOL64), ("f32", TOL32_STEPS)):
         g = gpu_sim(w, prec)
         g.init_equilibrium(rho, u[:, :2])
         g.step(k)
-        err = rel_err(deviation(g.get_populations()[:, centres], lat), deviation(want, lat))
-        print("%s sampled 2048^2 error %.3e" % (prec, err))
-        assert err < tol
+        check_close(deviation(g.get_populations()[:, centres], lat), deviation(want, lat), tol, None,
+                    "%s 2048^2 samples" % prec)
         del g
 
 
@@ -360,6 +356,5 @@ def test_full_size_d3q15_pipe_sampled_nodes():
     g = gpu_sim(w, "f32")
     g.init_equilibrium(rho, u)
     g.step(2)
-    err = rel_err(deviation(g.get_populations()[:, centres], lat), deviation(want, lat))
-    print("D3Q15 f32 sampled full-size error %.3e" % err)
-    assert err < 1e-5
+    check_close(deviation(g.get_populations()[:, centres], lat), deviation(want, lat), TOL32_STEPS,
+                None, "D3Q15 f32 L=256 samples")

@@ -11,7 +11,7 @@ from oracle import lbm as O
 from paper_1712_08288_gb300 import binding as B
 from paper_1712_08288_gb300 import workloads as W
 
-from gpu_common import deviation, gpu_sim, rel_err, require_gpu
+from gpu_common import check_close, deviation, gpu_sim, require_gpu
 
 pytestmark = pytest.mark.gpu
 TOL64 = 1e-12
@@ -44,7 +44,7 @@ def test_couette_two_node_matches_oracle(scheme, steps):
     o.step(steps)
     g.step(steps)
     fl = ~w["solid"]
-    assert rel_err(deviation(g.get_populations(), lat), deviation(o.f, lat), fl) < TOL64
+    check_close(deviation(g.get_populations(), lat), deviation(o.f, lat), TOL64, fl)
 
 
 @pytest.mark.parametrize("lattice", ["D3Q19", "D3Q15"])
@@ -60,7 +60,7 @@ def test_sphere_and_pipe_two_node_match_oracle(lattice):
         o.step(13)
         g.step(13)
         fl = ~w["solid"]
-        assert rel_err(deviation(g.get_populations(), lat), deviation(o.f, lat), fl) < TOL64
+        check_close(deviation(g.get_populations(), lat), deviation(o.f, lat), TOL64, fl)
 
 
 def test_fp32_two_node_bound():
@@ -73,9 +73,7 @@ def test_fp32_two_node_bound():
     fl = ~w["solid"]
     _, ug = g.moments()
     _, uo = o.moments()
-    err = rel_err(ug[fl][:, :2], uo[fl][:, :2])
-    print("two-node FP32 velocity error vs FP64 oracle: %.3e" % err)
-    assert err < 2e-6
+    check_close(ug[fl][:, :2], uo[fl][:, :2], 2e-6, None, "two-node f32 u")
 
 
 def test_two_node_poiseuille_second_order_and_switching_off():

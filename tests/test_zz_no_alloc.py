@@ -64,10 +64,13 @@ def test_noalloc_norms_match_allocating_entry_point(lattice, prec):
 
 
 def test_noalloc_rejects_grids_beyond_the_static_limit():
-    require_gpu()
+    torch = require_gpu()
     sim = B.Lbm("D3Q19", (324, 324, 324), W.relaxation_rates("D3Q19", 1.0), "f16")
+    out_dev = torch.full((7,), float("nan"), dtype=torch.float64, device="cuda")
     with pytest.raises(B.LbmError) as ei:
-        sim.error_norms_noalloc(0, 1 << 20)     # rejected before any device access
+        sim.error_norms_noalloc(0, out_dev.data_ptr())
     assert ei.value.code == -1
     assert "33,554,432 nodes" in str(ei.value)
+    torch.cuda.synchronize()
+    assert torch.isnan(out_dev).all()           # nothing was launched
     sim.close()
