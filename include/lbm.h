@@ -52,6 +52,9 @@
  *     host data synchronise that stream.
  *   - Device memory (populations, geometry) is allocated by the library with
  *     cudaMalloc on the device current at lbm_create, and freed by lbm_destroy.
+ *   - Every call that touches the GPU makes its context's (or batch's) device
+ *     current for its duration and restores the calling thread's current device
+ *     before it returns.
  */
 #ifndef LBM_H
 #define LBM_H
@@ -207,9 +210,24 @@ int lbm_error_norms(lbm_ctx *ctx, const double *u_ref, lbm_norms *out);
  * Limit: at most 33,554,432 nodes (e.g. 322^3); larger grids return LBM_EINVAL.
  * The first call on each device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents; calls
- * that overlap on the GPU race on it, so issue them in order on one stream. */
+ * capture.  The looked-up address is kept for the life of the process: after a
+ * cudaDeviceReset of that device it is stale, so do not call this entry point on
+ * a device that was reset.  All calls share the array and it keeps the last call's
+ * contents; calls that overlap on the GPU race on it, so issue them in order on one
+ * stream. */
 int lbm_error_norms_noalloc(lbm_ctx *ctx, const double *u_ref_dev, double *out_dev);
+
+/* Limit on the sweep's wait for a tile's bulk copies, in polls of the tile's
+ * barrier (each poll suspends for at most 1 ms); default 1000, about 1 s, far
+ * beyond any legitimate copy latency.  There is no counterpart in the paper: it
+ * is the failure-detection bound of the library's pipeline.  A warp whose wait
+ * runs out sets the context's status (read as LBM_ETIMEOUT by the next
+ * lbm_moments or lbm_error_norms), waits with the default limit for the copies it
+ * still has in flight and leaves the step unfinished; a new initial state
+ * (lbm_init_equilibrium or lbm_set_populations) clears the status.  polls = 0
+ * makes every sweep give up at its first wait, which exercises that path without
+ * any fault.  polls < 0 is LBM_EINVAL.  Batches use the default limit. */
+int lbm_set_wait_limit(lbm_ctx *ctx, int polls);
 
 /* Replace the relaxation rates (no reset of the populations). */
 int lbm_set_relaxation(lbm_ctx *ctx, const double *s);
@@ -242,6 +260,23 @@ int lbm_adjoint(lbm_ctx *ctx, int n_steps, int checkpoint_every, const uint8_t *
                 const double *u_target, double *loss, double *grad_s, double *grad_q,
                 double *grad_uw);
 
+/* lbm_adjoint in two halves, for a reverse-mode framework whose forward and
+ * backward calls are separate (lbm_adjoint is exactly the two in sequence).
+ * lbm_adjoint_forward runs the n_steps with checkpoints, keeps the tape (the
+ * checkpoints, the last segment's states, mask and u_target) in the context and
+ * returns J; its cost is that of lbm_step(n_steps) plus the checkpoint copies.
+ * lbm_adjoint_backward recomputes and runs the adjoint sweep from that tape and
+ * returns the gradients; the context ends in the forward run's end state, and the
+ * tape stays valid, so the backward pass may be repeated.  Any call that changes
+ * the populations or the arguments of the step in between (lbm_step,
+ * lbm_init_equilibrium, lbm_set_populations, lbm_set_geometry, lbm_set_relaxation,
+ * lbm_set_link_values, lbm_set_scheme, lbm_set_force, lbm_set_wall_factor, a batch
+ * step) discards the tape: lbm_adjoint_backward then returns LBM_ESTATE.  One tape
+ * per context; a new forward pass replaces it.  Arguments as for lbm_adjoint. */
+int lbm_adjoint_forward(lbm_ctx *ctx, int n_steps, int checkpoint_every, const uint8_t *mask,
+                        const double *u_target, double *loss);
+int lbm_adjoint_backward(lbm_ctx *ctx, double *grad_s, double *grad_q, double *grad_uw);
+
 /* Batches (ensembles of independent problems).  A batch advances several contexts
  * -- same lattice, precision and device, any sizes, geometries and parameters --
  * by ONE persistent sweep launch per time step that walks the tiles of all of them,
@@ -265,6 +300,15 @@ int lbm_batch_step(lbm_batch *batch, int n);
 int lbm_batch_query(const lbm_batch *batch, int *n_contexts, int64_t *tiles, int *order,
                     int *blocks_per_sm);
 const char *lbm_batch_last_error(const lbm_batch *batch);
+
+/* The current device's FP64 fused multiply-add rate in GFLOP/s (an FMA counted as
+ * two operations), measured with a plain timed FMA loop (8 independent chains per
+ * thread, every SM full).  There is no counterpart in the paper: it is the
+ * denominator against which the FP64 sweep, bound by the FP64 pipe rather than by
+ * HBM on this GPU, is reported.  Runs on the legacy stream and synchronises it;
+ * changes no device setting.  LBM_EINVAL for a NULL pointer, LBM_ECUDA if a CUDA
+ * call fails. */
+int lbm_probe_fp64_rate(double *gflops);
 
 /* Sizes: lattice Q and D, node counts, link count. */
 int lbm_query(const lbm_ctx *ctx, int *Q, int *D, int64_t *nodes, int64_t *fluid_nodes,

@@ -9,6 +9,23 @@
 
 namespace lbm {
 
+// Makes `dev` the current device for the lifetime of the object and restores the
+// caller's current device afterwards: entry points run on their context's device
+// without leaving the calling thread's device changed.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard &) = delete;
+  DeviceGuard &operator=(const DeviceGuard &) = delete;
+};
+
 // Tile width of the sweep: a warp handles kTileW consecutive nodes along x,
 // kNodesPerLane per lane.
 #ifndef LBM_NPL
@@ -70,6 +87,10 @@ struct alignas(4 * sizeof(C)) LinkCoef {
 constexpr long long kPopPadBytes = 4096;
 inline long long slot_stride(long long N) { return (N + 63) / 64 * 64; }
 
+// default number of barrier polls before a sweep gives up waiting for a copy
+// (each poll suspends for at most 1 ms: about 1 s in all)
+constexpr int kWaitLimitDefault = 1000;
+
 template <class C>
 struct SweepArgs {
   void *pop;                 // population i of node n at pop[i*S + n]
@@ -83,6 +104,7 @@ struct SweepArgs {
   C one_minus_b;
   C wfac;                    // factor on every link's wall velocity in this step
   int *status;               // bit 0: non-finite density seen, bit 1: bounded wait gave up
+  int wait_polls;            // polls of a tile's barrier before the sweep gives up
   // element offsets of the stores of an interior node: even step slot opp(i) of
   // the node itself, odd step slot i of x + e_i (no wrap)
   long long koff_even[19];

@@ -115,7 +115,12 @@ __global__ void noalloc_finish_kernel(const double *partials, int n_blocks, bool
   }
 }
 
-// device address of the scratch array, looked up once per device
+// Device address of the scratch array, looked up once per device ordinal with
+// that device current and kept for the life of the process.  The cache assumes
+// the device's primary context lives as long as the process: after
+// cudaDeviceReset (which unloads the library's device code and frees the array)
+// the cached address is stale, so a caller that resets a device must not use this
+// entry point on it again in the same process.
 std::mutex g_mu;
 double *g_scratch_addr[128] = {nullptr};
 
@@ -144,9 +149,9 @@ int error_norms_noalloc(int device, int lattice, int precision, const AuxArgs &a
     *why = "out_dev is NULL";
     return LBM_EINVAL;
   }
-  cudaError_t e = cudaSetDevice(device);
+  DeviceGuard dg(device);
   double *scratch = nullptr;
-  if (e == cudaSuccess) e = scratch_address(device, &scratch);
+  cudaError_t e = scratch_address(device, &scratch);
   if (e != cudaSuccess) {
     *why = cudaGetErrorString(e);
     return LBM_ECUDA;

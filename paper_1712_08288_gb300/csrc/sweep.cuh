@@ -26,6 +26,7 @@
 // and differences a_p = g_i - g_ib of opposite pairs.
 #pragma once
 
+#include <mutex>
 #include <type_traits>
 
 #include "common.cuh"
@@ -327,7 +328,7 @@ struct Neighbours {
 // count, cp.async.bulk global -> shared.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kSuspendHintNs = 1000000;   // 1 ms upper bound per poll
-constexpr int kWaitLimit = 1000;
+constexpr int kWaitLimit = kWaitLimitDefault;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -353,10 +354,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return done != 0;
 }
-// bounded wait: gives up after kWaitLimit polls, i.e. after about
-// kWaitLimit * kSuspendHintNs = 1 s, far beyond any legitimate copy latency
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-  for (int it = 0; it < kWaitLimit; ++it)
+// bounded wait: gives up after `polls` polls, each suspending for at most
+// kSuspendHintNs; the default kWaitLimit polls is about 1 s, far beyond any
+// legitimate copy latency
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  int polls = kWaitLimit) {
+  for (int it = 0; it < polls; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -574,9 +577,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
   int k = 0;
   for (int tile = gw; tile < n_tiles; tile += nw, ++k) {
     const int s = k % NS;
-    const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)(k / NS) & 1u);
+    // the detection wait is limited by the host-set a.wait_polls (lbm_set_wait_limit)
+    const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)(k / NS) & 1u, a.wait_polls);
     if (__any_sync(0xffffffffu, !ok)) {
-      // a copy did not land in time: flag it, drain what this warp issued, stop
+      // a copy did not land in time: flag it, then wait (with the long default
+      // limit) for every copy this warp still has in flight into its shared
+      // memory before leaving, and stop
       if (lane == 0) atomicOr(args_for<BATCH>(a, inst, tile_inst, tile).status, 2);
       for (int j = 0; j < NS; ++j)
         if (tile + j * nw < n_tiles) mbar_wait_bounded(&bars[(k + j) % NS], (uint32_t)((k + j) / NS) & 1u);
@@ -722,21 +728,27 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
   }
 }
 
-// Persistent grid size of one kernel instantiation (resident blocks per SM x
-// SMs), computed once per kernel; also raises the kernel's dynamic shared-memory
-// limit to what it uses.
+// Persistent grid size of one kernel instantiation on the current device
+// (resident blocks per SM x SMs).  The first call on each device also raises the
+// kernel's dynamic shared-memory limit there (a per-device function attribute) to
+// what it uses; both are cached per device ordinal.
+constexpr int kMaxDevices = 64;
 template <auto Kernel>
 int persistent_blocks(int threads, size_t smem) {
-  static int cached = 0;
-  if (cached == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
+  static std::mutex mu;
+  static int cached[kMaxDevices] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= kMaxDevices) dev = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  if (cached[dev] == 0) {
+    int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, Kernel, threads, smem);
-    cached = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    cached[dev] = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
   }
-  return cached;
+  return cached[dev];
 }
 
 template <auto Kernel, class A>
@@ -794,6 +806,7 @@ cudaError_t launch_sweep_batch_t(bool odd, const SweepArgs<typename Storage<T>::
   using A = SweepArgs<typename Storage<T>::C>;
   const size_t smem = kWarpsPerBlock * warp_smem_bytes<L, T>();
   A dummy{};
+  dummy.wait_polls = kWaitLimit;
 #define LBM_LAUNCH_B(O, I)                                                                       \
   launch_persistent<sweep_kernel<L, T, O, true, false, I, true>>(dummy, tiles, n_tiles, smem, st, \
                                                                  inst, tile_inst, blocks_per_sm, \
