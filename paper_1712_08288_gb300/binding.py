@@ -26,7 +26,8 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_set_skew", "lbm_s
            "lbm_set_scheme", "lbm_set_force", "lbm_set_wall_factor", "lbm_set_two_node", "lbm_init_equilibrium", "lbm_set_populations",
            "lbm_get_populations", "lbm_step", "lbm_time", "lbm_moments", "lbm_moments_device",
            "lbm_error_norms", "lbm_error_norms_noalloc", "lbm_query", "lbm_last_error",
-           "lbm_set_relaxation", "lbm_set_link_values", "lbm_adjoint",
+           "lbm_set_relaxation", "lbm_set_link_values", "lbm_set_wait_limit", "lbm_adjoint",
+           "lbm_adjoint_forward", "lbm_adjoint_backward", "lbm_probe_fp64_rate",
            "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_set_stream", "lbm_batch_set_config",
            "lbm_batch_tune", "lbm_batch_step", "lbm_batch_query", "lbm_batch_last_error"]
 
@@ -64,7 +65,11 @@ def load_library(path=LIB_PATH):
         "lbm_last_error": (ct.c_char_p, [P]),
         "lbm_set_relaxation": (I, [P, P]),
         "lbm_set_link_values": (I, [P, P, P]),
+        "lbm_set_wait_limit": (I, [P, I]),
         "lbm_adjoint": (I, [P, I, I, P, P, P, P, P, P]),
+        "lbm_adjoint_forward": (I, [P, I, I, P, P, P]),
+        "lbm_adjoint_backward": (I, [P, P, P, P]),
+        "lbm_probe_fp64_rate": (I, [P]),
         "lbm_batch_create": (I, [ct.POINTER(P), I, P]),
         "lbm_batch_destroy": (I, [P]),
         "lbm_batch_set_stream": (I, [P, P]),
@@ -217,6 +222,10 @@ class Lbm:
         self._check(self._lib.lbm_error_norms_noalloc(self.h, ct.c_void_p(u_ref_dev_ptr),
                                                       ct.c_void_p(out_dev_ptr)))
 
+    def set_wait_limit(self, polls):
+        """lbm_set_wait_limit: barrier polls before a sweep gives up (default 1000)."""
+        self._check(self._lib.lbm_set_wait_limit(self.h, int(polls)))
+
     def set_relaxation(self, s):
         s = np.ascontiguousarray(s, dtype=np.float64)
         assert s.shape == (self.Q,)
@@ -240,6 +249,24 @@ class Lbm:
                                           ct.byref(J), _ptr(gs), _ptr(gq), _ptr(gp)))
         return J.value, gs, gq, gp
 
+    def adjoint_forward(self, n_steps, mask, u_target, checkpoint_every=0):
+        """lbm_adjoint_forward: the checkpointed run; returns J and keeps the tape."""
+        mask = np.ascontiguousarray(np.asarray(mask).reshape(self.N), dtype=np.uint8)
+        ut = np.ascontiguousarray(np.asarray(u_target, dtype=np.float64).reshape(self.N, -1)[:, : self.D])
+        J = ct.c_double()
+        self._check(self._lib.lbm_adjoint_forward(self.h, int(n_steps), int(checkpoint_every), _ptr(mask),
+                                                  _ptr(ut), ct.byref(J)))
+        return J.value
+
+    def adjoint_backward(self):
+        """lbm_adjoint_backward: (dJ/ds (Q,), dJ/dq (links,), dJ/dphi (links, 3)) from the tape."""
+        nl = self.query()["links"]
+        gs = np.zeros(self.Q)
+        gq = np.zeros(nl)
+        gp = np.zeros((nl, 3))
+        self._check(self._lib.lbm_adjoint_backward(self.h, _ptr(gs), _ptr(gq), _ptr(gp)))
+        return gs, gq, gp
+
     def query(self):
         Q, D = ct.c_int(), ct.c_int()
         n, nf, nl = ct.c_int64(), ct.c_int64(), ct.c_int64()
@@ -248,31 +275,54 @@ class Lbm:
         return dict(Q=Q.value, D=D.value, nodes=n.value, fluid_nodes=nf.value, links=nl.value)
 
 
+def probe_fp64_rate():
+    """lbm_probe_fp64_rate: the current device's FP64 FMA rate in GFLOP/s."""
+    g = ct.c_double()
+    rc = lib().lbm_probe_fp64_rate(ct.byref(g))
+    if rc != 0:
+        raise LbmError(rc, "lbm_probe_fp64_rate failed")
+    return g.value
+
+
 def adjoint_loss_function():
-    """A torch.autograd.Function whose forward runs n_steps from a fixed initial state
-    and returns J = sum_mask |u(T) - u_target|^2, and whose backward returns the
-    gradients the library's adjoint computed (dJ/dq per link, dJ/ds, dJ/dphi).
+    """A torch.autograd.Function for J = sum_mask |u(T) - u_target|^2 after n_steps
+    from a fixed initial state.  forward runs lbm_adjoint_forward (the checkpointed
+    run: the cost of the n_steps plus the checkpoint copies) and returns J;
+    backward runs lbm_adjoint_backward (recompute and adjoint sweep) and returns
+    gJ * dJ/dq per link, gJ * dJ/ds and gJ * dJ/dphi on the inputs' devices and
+    dtypes.
 
     apply(q, s, uw, sim, f0, n_steps, mask, u_target, checkpoint_every) with q
-    (links,), s (Q,), uw (links, 3) float64 tensors; f0 the initial full populations
-    (Q, nodes) numpy array the run starts from.
+    (links,), s (Q,), uw (links, 3) tensors (any device; their values are copied to
+    the context); f0 the initial full populations (Q, nodes) numpy array the run
+    starts from.  The context holds one tape: stepping or changing it between
+    forward and backward makes backward raise (LBM_ESTATE).  J is returned on q's
+    device in float64.
     """
     import torch
 
     class AdjointLoss(torch.autograd.Function):
         @staticmethod
         def forward(ctx, q, s, uw, sim, f0, n_steps, mask, u_target, checkpoint_every=0):
-            sim.set_relaxation(s.detach().cpu().numpy())
-            sim.set_link_values(q.detach().cpu().numpy(), uw.detach().cpu().numpy())
+            sim.set_relaxation(s.detach().to("cpu", torch.float64).numpy())
+            sim.set_link_values(q.detach().to("cpu", torch.float64).numpy(),
+                                uw.detach().to("cpu", torch.float64).numpy())
             sim.set_populations(f0)
-            J, gs, gq, gp = sim.adjoint(n_steps, mask, u_target, checkpoint_every)
-            ctx.save_for_backward(torch.from_numpy(gq), torch.from_numpy(gs), torch.from_numpy(gp))
-            return torch.tensor(J, dtype=torch.float64)
+            J = sim.adjoint_forward(n_steps, mask, u_target, checkpoint_every)
+            ctx.sim = sim
+            ctx.like = (q, s, uw)
+            return torch.tensor(J, dtype=torch.float64, device=q.device)
 
         @staticmethod
         def backward(ctx, gJ):
-            gq, gs, gp = ctx.saved_tensors
-            return gJ * gq, gJ * gs, gJ * gp, None, None, None, None, None, None
+            gs, gq, gp = ctx.sim.adjoint_backward()
+            q, s, uw = ctx.like
+            g = gJ.detach().to("cpu", torch.float64)
+            out = []
+            for grad, like in ((gq, q), (gs, s), (gp, uw)):
+                t = g * torch.from_numpy(grad.reshape(tuple(like.shape)))
+                out.append(t.to(like.device, like.dtype))
+            return (out[0], out[1], out[2], None, None, None, None, None, None)
 
     return AdjointLoss
 

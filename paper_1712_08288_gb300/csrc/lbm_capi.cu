@@ -45,6 +45,17 @@ cudaError_t launch_sweep(int lattice, int precision, bool odd, const SweepArgs<d
 
 using namespace lbm;
 
+// What a forward pass of the adjoint leaves for the backward pass: its start time,
+// length, checkpoint interval and checkpoint times, and the identity of the state
+// it ended in (state serial and argument version), which the backward pass checks.
+struct AdjTape {
+  bool valid = false;
+  bool last_saved = false;      // the last segment's states are still in the workspace
+  long long t0 = 0, T = 0, K = 0, nseg = 0;
+  std::vector<long long> tck;
+  long long serial = -1, version = -1;
+};
+
 struct lbm_ctx {
   int lattice = 0, Q = 0, D = 0, precision = 0;
   int nx = 0, ny = 0, nz = 0, sy = 0, sz = 0;
@@ -57,6 +68,7 @@ struct lbm_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   long long t = 0;
+  int wait_polls = kWaitLimitDefault;  // lbm_set_wait_limit
   double wf_a0 = 1.0, wf_r = 1.0;  // wall-velocity factor a0 r^(t - wf_t0)
   long long wf_t0 = 0;
   bool geometry_set = false;
@@ -94,6 +106,8 @@ struct lbm_ctx {
   std::vector<int64_t> link_src; // input position of the link at each device position
   // device workspace of lbm_adjoint (pointer, capacity), kept between calls
   std::pair<void *, size_t> adj_ws[13] = {};
+  AdjTape tape;                 // what lbm_adjoint_forward left for the backward pass
+  long long state_serial = 0;   // bumped by every call that changes the populations
   long long n_links = 0, n_fluid = 0, n_boundary = 0;
 
   SweepArgs<double> a64;
@@ -200,6 +214,7 @@ static void refresh_args(lbm_ctx *c) {
     a.one_minus_b = C(1.0 - c->b);
     a.wfac = C(wall_factor(c, c->t));
     a.status = c->status;
+    a.wait_polls = c->wait_polls;
     with_lat(c->lattice, [&](auto lat) {
       using L = decltype(lat);
       const long long S = slot_stride(c->N), nxl = c->nx, nxy = (long long)c->nx * c->ny;
@@ -280,6 +295,7 @@ static cudaError_t adj_ws_get(lbm_ctx *c, int slot, size_t bytes, void **p) {
   return cudaSuccess;
 }
 static void adj_ws_free(lbm_ctx *c) {
+  c->tape.valid = false;
   for (auto &e : c->adj_ws) {
     cudaFree(e.first);
     e = {nullptr, 0};
@@ -446,7 +462,7 @@ int lbm_create(lbm_ctx **out, int lattice, int nx, int ny, int nz, const double 
 
 int lbm_destroy(lbm_ctx *c) {
   if (!c) return LBM_OK;
-  cudaSetDevice(c->device);
+  DeviceGuard dg(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   cudaFree(c->pop_alloc);
   cudaFree(c->cls);
@@ -490,7 +506,7 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *solid, int64_t n_links, const in
   if (!solid) return fail(c, LBM_EINVAL, "lbm_set_geometry: solid is NULL");
   if (n_links < 0 || (n_links > 0 && (!node || !dir || !q)))
     return fail(c, LBM_EINVAL, "lbm_set_geometry: bad link arrays");
-  cudaSetDevice(c->device);
+  DeviceGuard dg(c->device);
   const long long N = c->N;
   const int Q = c->Q;
   int rc = LBM_OK;
@@ -618,6 +634,7 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *solid, int64_t n_links, const in
   cudaFree(c->u_prev);
   c->u_prev = nullptr;
   c->t = 0;
+  ++c->state_serial;
   c->geometry_set = true;
   refresh_args(c);
   return build_two_node(c);
@@ -626,7 +643,7 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *solid, int64_t n_links, const in
 int lbm_set_two_node(lbm_ctx *c, int enable) {
   if (!c) return LBM_EINVAL;
   if (!c->geometry_set) return fail(c, LBM_ESTATE, "lbm_set_two_node: geometry not set");
-  cudaSetDevice(c->device);
+  DeviceGuard dg(c->device);
   c->two_node = enable != 0;
   ++c->version;
   return build_two_node(c);
@@ -654,7 +671,7 @@ int lbm_set_scheme(lbm_ctx *c, double c0, double c1, double c2, double b, int al
     }
   c->c0 = c0; c->c1 = c1; c->c2 = c2; c->b = b;
   c->allow_nonconvex = allow_nonconvex != 0;
-  cudaSetDevice(c->device);
+  DeviceGuard dg(c->device);
   int rc = upload_coefficients(c);
   refresh_args(c);
   return rc;
@@ -672,6 +689,14 @@ int lbm_set_wall_factor(lbm_ctx *c, double a0, double r) {
   return LBM_OK;
 }
 
+int lbm_set_wait_limit(lbm_ctx *c, int polls) {
+  if (!c) return LBM_EINVAL;
+  if (polls < 0) return fail(c, LBM_EINVAL, "lbm_set_wait_limit: polls = %d < 0", polls);
+  c->wait_polls = polls;
+  refresh_args(c);
+  return LBM_OK;
+}
+
 int lbm_set_force(lbm_ctx *c, const double g[3]) {
   if (!c || !g) return LBM_EINVAL;
   for (int k = 0; k < 3; ++k)
@@ -684,7 +709,7 @@ int lbm_set_force(lbm_ctx *c, const double g[3]) {
 int lbm_init_equilibrium(lbm_ctx *c, const double *rho, const double *u) {
   if (!c) return LBM_EINVAL;
   if (!c->geometry_set) return fail(c, LBM_ESTATE, "lbm_init_equilibrium: geometry not set");
-  cudaSetDevice(c->device);
+  DeviceGuard dg(c->device);
   // staging buffers are the context's moment buffers (same sizes), kept for reuse
   if (rho) {
     if (!c->mom_rho) CUDA_OR_FAIL(c, cudaMalloc(&c->mom_rho, sizeof(double) * c->N));
@@ -702,13 +727,14 @@ int lbm_init_equilibrium(lbm_ctx *c, const double *rho, const double *u) {
   CUDA_OR_FAIL(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
   CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
   c->t = 0;
+  ++c->state_serial;
   return LBM_OK;
 }
 
 int lbm_set_populations(lbm_ctx *c, const double *f) {
   if (!c || !f) return LBM_EINVAL;
   if (!c->geometry_set) return fail(c, LBM_ESTATE, "lbm_set_populations: geometry not set");
-  cudaSetDevice(c->device);
+  DeviceGuard dg(c->device);
   double *df = nullptr;
   const size_t bytes = sizeof(double) * c->Q * c->N;
   CUDA_OR_FAIL(c, cudaMalloc(&df, bytes));
@@ -718,12 +744,13 @@ int lbm_set_populations(lbm_ctx *c, const double *f) {
   cudaFree(df);
   CUDA_OR_FAIL(c, cudaMemset(c->status, 0, sizeof(int)));
   c->t = 0;
+  ++c->state_serial;
   return LBM_OK;
 }
 
 int lbm_get_populations(lbm_ctx *c, double *f) {
   if (!c || !f) return LBM_EINVAL;
-  cudaSetDevice(c->device);
+  DeviceGuard dg(c->device);
   double *df = nullptr;
   const size_t bytes = sizeof(double) * c->Q * c->N;
   CUDA_OR_FAIL(c, cudaMalloc(&df, bytes));
@@ -739,6 +766,7 @@ int lbm_step(lbm_ctx *c, int n) {
   if (!c) return LBM_EINVAL;
   if (n < 0) return fail(c, LBM_EINVAL, "lbm_step: n = %d < 0", n);
   if (!c->geometry_set) return fail(c, LBM_ESTATE, "lbm_step: geometry not set");
+  DeviceGuard dg(c->device);
   for (int k = 0; k < n; ++k) {
     set_step_factor(c, c->t);
     const bool odd = (c->t & 1) != 0;
@@ -754,6 +782,7 @@ int lbm_step(lbm_ctx *c, int n) {
                           c->n_tn, c->tn_delta, c->stream);
     if (e != cudaSuccess) return fail(c, LBM_ECUDA, "lbm_step: %s", cudaGetErrorString(e));
     ++c->t;
+    ++c->state_serial;
   }
   return LBM_OK;
 }
@@ -771,7 +800,7 @@ static int check_status(lbm_ctx *c) {
 
 int lbm_moments_device(lbm_ctx *c, double *rho_dev, double *u_dev) {
   if (!c) return LBM_EINVAL;
-  cudaSetDevice(c->device);
+  DeviceGuard dg(c->device);
   CUDA_OR_FAIL(c, launch_moments(c->lattice, c->precision, aux_args(c), (c->t & 1) != 0, rho_dev,
                                  u_dev, c->stream));
   return LBM_OK;
@@ -779,7 +808,7 @@ int lbm_moments_device(lbm_ctx *c, double *rho_dev, double *u_dev) {
 
 int lbm_moments(lbm_ctx *c, double *rho, double *u) {
   if (!c) return LBM_EINVAL;
-  cudaSetDevice(c->device);
+  DeviceGuard dg(c->device);
   if (rho && !c->mom_rho) CUDA_OR_FAIL(c, cudaMalloc(&c->mom_rho, sizeof(double) * c->N));
   if (u && !c->mom_u) CUDA_OR_FAIL(c, cudaMalloc(&c->mom_u, sizeof(double) * c->N * c->D));
   int rc = lbm_moments_device(c, rho ? c->mom_rho : nullptr, u ? c->mom_u : nullptr);
@@ -796,7 +825,7 @@ int lbm_moments(lbm_ctx *c, double *rho, double *u) {
 
 int lbm_error_norms(lbm_ctx *c, const double *u_ref, lbm_norms *out) {
   if (!c || !out) return LBM_EINVAL;
-  cudaSetDevice(c->device);
+  DeviceGuard dg(c->device);
   const int nb = norm_blocks_for(c->N);
   if (!c->partials) CUDA_OR_FAIL(c, cudaMalloc(&c->partials, sizeof(double) * kNormFields * nb));
   if (!c->norm_out) CUDA_OR_FAIL(c, cudaMalloc(&c->norm_out, sizeof(double) * kNormFields));
@@ -870,23 +899,31 @@ int lbm_set_link_values(lbm_ctx *c, const double *q, const double *uw) {
   }
   c->link_q.swap(nq);
   c->link_uw.swap(nuw);
-  cudaSetDevice(c->device);
+  DeviceGuard dg(c->device);
   const int rc = upload_coefficients(c);
   refresh_args(c);
   return rc;
 }
 
-int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *mask,
-                const double *u_target, double *loss, double *grad_s, double *grad_q,
-                double *grad_uw) {
-  if (!c) return LBM_EINVAL;
+// ---------------------------------------------------------------------------
+// Discrete adjoint, split into a forward pass (checkpointed run and the loss) and
+// a backward pass (recompute and adjoint sweep).  The tape between them lives in
+// the context: the workspace buffers, the checkpoint times and the identity of
+// the state the forward pass ended in.
+// ---------------------------------------------------------------------------
+namespace {
+// workspace slots (lbm_ctx::adj_ws)
+enum AdjSlot { kCk = 0, kSeg, kFin, kLam0, kLam1, kMask, kUt, kGs, kTot, kAcc, kDcoef, kJ, kGpart };
+
+int adjoint_forward_impl(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *mask,
+                         const double *u_target, double *loss) {
+  c->tape.valid = false;
   if (n_steps < 1) return fail(c, LBM_EINVAL, "lbm_adjoint: n_steps >= 1");
   if (!mask || !u_target) return fail(c, LBM_EINVAL, "lbm_adjoint: mask and u_target are required");
   if (checkpoint_every < 0) return fail(c, LBM_EINVAL, "lbm_adjoint: checkpoint_every < 0");
   if (c->two_node)
     return fail(c, LBM_ESTATE, "lbm_adjoint: differentiates the single-node scheme; two-node is on");
   if (!c->geometry_set) return fail(c, LBM_ESTATE, "lbm_adjoint: geometry not set");
-  cudaSetDevice(c->device);
   const long long T = n_steps;
   long long K = checkpoint_every;
   if (K == 0) K = (long long)std::ceil(std::sqrt((double)T));
@@ -896,51 +933,135 @@ int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *ma
   const size_t state = (size_t)c->Q * c->N * csize;               // natural layout, compute type
   const size_t raw_pop = pop_alloc_bytes(c);
   const size_t raw_lnk = (size_t)store_bytes(c->precision) * std::max<long long>(1, c->n_links);
-  const long long nl = c->n_links;
+  const long long nl1 = std::max<long long>(1, c->n_links);
+  const bool natural = c->precision == LBM_F64 || c->precision == LBM_F32_DEV;
+  const size_t ck_bytes = natural ? state : raw_pop + raw_lnk;
   char *ck = nullptr, *seg = nullptr, *fin = nullptr, *lam0 = nullptr, *lam1 = nullptr;
   uint8_t *dmask = nullptr;
-  double *dut = nullptr, *dgs = nullptr, *dtot = nullptr, *dJ = nullptr;
-  double *gpart = nullptr;
-  void *dcoef = nullptr, *acc = nullptr;
-  const long long pblocks = adjoint_partial_blocks(c->N);
-  std::vector<long long> tck(nseg);
-  int rc = LBM_OK;
-  // on failure the workspace is released; on success it stays for the next call
-  bool ok = false;
-  auto cleanup = [&]() {
-    if (!ok) adj_ws_free(c);
-    c->a64.save = nullptr;
-    c->a32.save = nullptr;
-  };
+  double *dut = nullptr, *dJ = nullptr;
+  void *p = nullptr;
 #define ADJ_CUDA(call)                                                                      \
   do {                                                                                      \
     cudaError_t e_ = (call);                                                                \
     if (e_ != cudaSuccess) {                                                                \
-      cleanup();                                                                            \
+      c->a64.save = nullptr;                                                                \
+      c->a32.save = nullptr;                                                                \
+      adj_ws_free(c);                                                                       \
       return fail(c, e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s", #call, \
                   cudaGetErrorString(e_));                                                  \
     }                                                                                       \
   } while (0)
-  const long long nl1 = std::max<long long>(1, nl);
-  ADJ_CUDA(adj_ws_get(c, 0, (c->precision == LBM_F64 || c->precision == LBM_F32_DEV
-                                 ? state : raw_pop + raw_lnk) * nseg, (void **)&ck));
-  ADJ_CUDA(adj_ws_get(c, 1, state * K, (void **)&seg));
-  ADJ_CUDA(adj_ws_get(c, 2, raw_pop + raw_lnk, (void **)&fin));
-  ADJ_CUDA(adj_ws_get(c, 3, state, (void **)&lam0));
-  ADJ_CUDA(adj_ws_get(c, 4, state, (void **)&lam1));
-  ADJ_CUDA(adj_ws_get(c, 5, c->N, (void **)&dmask));
-  ADJ_CUDA(adj_ws_get(c, 6, sizeof(double) * c->N * c->D, (void **)&dut));
-  ADJ_CUDA(adj_ws_get(c, 7, sizeof(double) * 19, (void **)&dgs));
-  ADJ_CUDA(adj_ws_get(c, 8, sizeof(double) * 2 * nl1, (void **)&dtot));
-  ADJ_CUDA(adj_ws_get(c, 9, csize * 2 * nl1, &acc));
-  ADJ_CUDA(adj_ws_get(c, 10, csize * 4 * nl1, &dcoef));
-  ADJ_CUDA(adj_ws_get(c, 11, sizeof(double), (void **)&dJ));
-  ADJ_CUDA(adj_ws_get(c, 12, sizeof(double) * c->Q * pblocks, (void **)&gpart));
+  const long long pblocks = adjoint_partial_blocks(c->N);
+  ADJ_CUDA(adj_ws_get(c, kCk, ck_bytes * nseg, (void **)&ck));
+  ADJ_CUDA(adj_ws_get(c, kSeg, state * K, (void **)&seg));
+  ADJ_CUDA(adj_ws_get(c, kFin, raw_pop + raw_lnk, (void **)&fin));
+  ADJ_CUDA(adj_ws_get(c, kLam0, state, (void **)&lam0));
+  ADJ_CUDA(adj_ws_get(c, kLam1, state, (void **)&lam1));
+  ADJ_CUDA(adj_ws_get(c, kMask, c->N, (void **)&dmask));
+  ADJ_CUDA(adj_ws_get(c, kUt, sizeof(double) * c->N * c->D, (void **)&dut));
+  ADJ_CUDA(adj_ws_get(c, kGs, sizeof(double) * 19, &p));
+  ADJ_CUDA(adj_ws_get(c, kTot, sizeof(double) * 2 * nl1, &p));
+  ADJ_CUDA(adj_ws_get(c, kAcc, csize * 2 * nl1, &p));
+  ADJ_CUDA(adj_ws_get(c, kDcoef, csize * 4 * nl1, &p));
+  ADJ_CUDA(adj_ws_get(c, kJ, sizeof(double), (void **)&dJ));
+  ADJ_CUDA(adj_ws_get(c, kGpart, sizeof(double) * c->Q * pblocks, &p));
   cudaStream_t st = c->stream;
-  ADJ_CUDA(cudaMemsetAsync(gpart, 0, sizeof(double) * c->Q * pblocks, st));
-  ADJ_CUDA(cudaMemsetAsync(lam1, 0, state, st));        // solid entries stay zero
   ADJ_CUDA(cudaMemcpyAsync(dmask, mask, c->N, cudaMemcpyHostToDevice, st));
   ADJ_CUDA(cudaMemcpyAsync(dut, u_target, sizeof(double) * c->N * c->D, cudaMemcpyHostToDevice, st));
+  ADJ_CUDA(cudaMemsetAsync(dJ, 0, sizeof(double), st));
+  AdjTape &tp = c->tape;
+  tp.t0 = c->t;
+  tp.T = T;
+  tp.K = K;
+  tp.nseg = nseg;
+  tp.tck.assign(nseg, 0);
+  // steps of a segment that also write each step's pre-collision state
+  auto step_saving = [&](int len) -> int {
+    for (int r = 0; r < len; ++r) {
+      if (c->precision == LBM_F64) c->a64.save = reinterpret_cast<double *>(seg + state * r);
+      else c->a32.save = reinterpret_cast<float *>(seg + state * r);
+      const int e = lbm_step(c, 1);
+      c->a64.save = nullptr;
+      c->a32.save = nullptr;
+      if (e != LBM_OK) return e;
+    }
+    return LBM_OK;
+  };
+  auto save_raw = [&](char *dst) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(dst, c->pop_alloc, raw_pop, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && c->lnk) e = cudaMemcpyAsync(dst + raw_pop, c->lnk, raw_lnk, cudaMemcpyDeviceToDevice, st);
+    return e;
+  };
+  // FP64 and FP32 storage keep natural-layout checkpoints (the backward pass
+  // recomputes with the push-form step); 16-bit storage keeps raw ones (it
+  // recomputes with the sweep itself, so that its rounding matches this run).  The
+  // last segment keeps its states as it goes, so the backward pass need not
+  // recompute it.
+  for (long long sgm = 0; sgm < nseg; ++sgm) {
+    if (natural)
+      ADJ_CUDA(launch_export_state(c->lattice, c->precision, aux_args(c), (c->t & 1) != 0,
+                                   ck + ck_bytes * sgm, st));
+    else
+      ADJ_CUDA(save_raw(ck + ck_bytes * sgm));
+    tp.tck[sgm] = c->t;
+    const int len = (int)std::min(K, T - sgm * K);
+    const int rc = sgm == nseg - 1 ? step_saving(len) : lbm_step(c, len);
+    if (rc != LBM_OK) { adj_ws_free(c); return rc; }
+  }
+  ADJ_CUDA(save_raw(fin));
+  // the loss (its kernel also writes lambda(T), which the backward pass recomputes)
+  ADJ_CUDA(cudaMemsetAsync(lam1, 0, state, st));
+  ADJ_CUDA(launch_export_state(c->lattice, c->precision, aux_args(c), (c->t & 1) != 0, lam1, st));
+  ADJ_CUDA(launch_loss(c->lattice, c->precision, aux_args(c), lam1, dmask, dut, lam0, dJ, st));
+  double hJ = 0.0;
+  ADJ_CUDA(cudaMemcpyAsync(&hJ, dJ, sizeof(double), cudaMemcpyDeviceToHost, st));
+  ADJ_CUDA(cudaStreamSynchronize(st));
+  if (loss) *loss = hJ;
+  const int rc = check_status(c);
+  if (rc != LBM_OK) return rc;
+  tp.version = c->version;
+  tp.serial = c->state_serial;
+  tp.valid = true;
+  tp.last_saved = true;
+  return LBM_OK;
+}
+
+int adjoint_backward_impl(lbm_ctx *c, double *grad_s, double *grad_q, double *grad_uw) {
+  AdjTape &tp = c->tape;
+  if (!tp.valid || tp.serial != c->state_serial || tp.version != c->version || c->t != tp.t0 + tp.T)
+    return fail(c, LBM_ESTATE,
+                "lbm_adjoint_backward: no forward pass for the current state (call "
+                "lbm_adjoint_forward; stepping or changing the context in between discards it)");
+  const long long T = tp.T, K = tp.K, nseg = tp.nseg;
+  const size_t csize = c->precision == LBM_F64 ? sizeof(double) : sizeof(float);
+  const size_t state = (size_t)c->Q * c->N * csize;
+  const size_t raw_pop = pop_alloc_bytes(c);
+  const size_t raw_lnk = (size_t)store_bytes(c->precision) * std::max<long long>(1, c->n_links);
+  const long long nl = c->n_links;
+  const long long nl1 = std::max<long long>(1, nl);
+  const bool natural = c->precision == LBM_F64 || c->precision == LBM_F32_DEV;
+  const size_t ck_bytes = natural ? state : raw_pop + raw_lnk;
+  const long long pblocks = adjoint_partial_blocks(c->N);
+  char *ck = static_cast<char *>(c->adj_ws[kCk].first), *seg = static_cast<char *>(c->adj_ws[kSeg].first);
+  char *fin = static_cast<char *>(c->adj_ws[kFin].first);
+  char *lam0 = static_cast<char *>(c->adj_ws[kLam0].first), *lam1 = static_cast<char *>(c->adj_ws[kLam1].first);
+  double *dgs = static_cast<double *>(c->adj_ws[kGs].first), *dtot = static_cast<double *>(c->adj_ws[kTot].first);
+  void *acc = c->adj_ws[kAcc].first, *dcoef = c->adj_ws[kDcoef].first;
+  double *gpart = static_cast<double *>(c->adj_ws[kGpart].first);
+  cudaStream_t st = c->stream;
+  tp.valid = false;   // reset below once the state is restored
+  const uint8_t *dmask = static_cast<const uint8_t *>(c->adj_ws[kMask].first);
+  const double *dut = static_cast<const double *>(c->adj_ws[kUt].first);
+  double *dJ = static_cast<double *>(c->adj_ws[kJ].first);
+  // lambda(T) from the forward end state (the current state): the state goes
+  // through lam1, which the first adjoint step overwrites; solid entries of both
+  // adjoint arrays stay zero
+  ADJ_CUDA(cudaMemsetAsync(lam0, 0, state, st));
+  ADJ_CUDA(cudaMemsetAsync(lam1, 0, state, st));
+  ADJ_CUDA(cudaMemsetAsync(dJ, 0, sizeof(double), st));
+  ADJ_CUDA(launch_export_state(c->lattice, c->precision, aux_args(c), (c->t & 1) != 0, lam1, st));
+  ADJ_CUDA(launch_loss(c->lattice, c->precision, aux_args(c), lam1, dmask, dut, lam0, dJ, st));
+  ADJ_CUDA(cudaMemsetAsync(gpart, 0, sizeof(double) * c->Q * pblocks, st));
   ADJ_CUDA(cudaMemsetAsync(dgs, 0, sizeof(double) * 19, st));
   ADJ_CUDA(cudaMemsetAsync(dtot, 0, sizeof(double) * 2 * nl1, st));
   ADJ_CUDA(cudaMemsetAsync(acc, 0, csize * 2 * nl1, st));
@@ -955,24 +1076,17 @@ int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *ma
   }
   if (c->precision == LBM_F64) {
     ADJ_CUDA(cudaMemcpyAsync(dcoef, hdc.data(), sizeof(double) * hdc.size(), cudaMemcpyHostToDevice, st));
+    ADJ_CUDA(cudaStreamSynchronize(st));     // hdc is about to go out of scope
   } else {
     std::vector<float> fdc(hdc.begin(), hdc.end());
     ADJ_CUDA(cudaMemcpyAsync(dcoef, fdc.data(), sizeof(float) * fdc.size(), cudaMemcpyHostToDevice, st));
     ADJ_CUDA(cudaStreamSynchronize(st));     // fdc is about to go out of scope
   }
-  ADJ_CUDA(cudaMemsetAsync(dJ, 0, sizeof(double), st));
-  auto save_raw = [&](char *dst) -> cudaError_t {
-    cudaError_t e = cudaMemcpyAsync(dst, c->pop_alloc, raw_pop, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess && c->lnk) e = cudaMemcpyAsync(dst + raw_pop, c->lnk, raw_lnk, cudaMemcpyDeviceToDevice, st);
-    return e;
-  };
   auto load_raw = [&](const char *src) -> cudaError_t {
     cudaError_t e = cudaMemcpyAsync(c->pop_alloc, src, raw_pop, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess && c->lnk) e = cudaMemcpyAsync(c->lnk, src + raw_pop, raw_lnk, cudaMemcpyDeviceToDevice, st);
     return e;
   };
-  const long long t0 = c->t;
-  // steps of a segment that also write each step's pre-collision state
   auto step_saving = [&](int len) -> int {
     for (int r = 0; r < len; ++r) {
       if (c->precision == LBM_F64) c->a64.save = reinterpret_cast<double *>(seg + state * r);
@@ -984,55 +1098,35 @@ int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *ma
     }
     return LBM_OK;
   };
-  // FP64 and FP32 storage (storage type = compute type) recompute segments with the
-  // push-form step in the natural layout, from natural-layout checkpoints: a step
-  // then reads and writes Q values per node instead of the sweep's three.  16-bit
-  // storage recomputes with the sweep itself, from raw checkpoints, so that its
-  // rounding matches the forward run.
-  const bool natural = c->precision == LBM_F64 || c->precision == LBM_F32_DEV;
-  const size_t ck_bytes = natural ? state : raw_pop + raw_lnk;
-  // forward pass with checkpoints every K steps; the last segment keeps its states
-  // as it goes, so the backward pass need not recompute it
-  for (long long sgm = 0; sgm < nseg; ++sgm) {
-    if (natural)
-      ADJ_CUDA(launch_export_state(c->lattice, c->precision, aux_args(c), (c->t & 1) != 0,
-                                   ck + ck_bytes * sgm, st));
-    else
-      ADJ_CUDA(save_raw(ck + ck_bytes * sgm));
-    tck[sgm] = c->t;
-    const int len = (int)std::min(K, T - sgm * K);
-    rc = sgm == nseg - 1 ? step_saving(len) : lbm_step(c, len);
-    if (rc != LBM_OK) { cleanup(); return rc; }
-  }
-  ADJ_CUDA(save_raw(fin));
-  // loss and lambda(T) (the final state goes through lam1, which the first adjoint
-  // step overwrites)
-  ADJ_CUDA(launch_export_state(c->lattice, c->precision, aux_args(c), (c->t & 1) != 0, lam1, st));
-  ADJ_CUDA(launch_loss(c->lattice, c->precision, aux_args(c), lam1, dmask, dut, lam0, dJ, st));
-  // backward pass: recompute each earlier segment from its checkpoint, then step back
+  // backward pass: recompute each segment from its checkpoint (the last one only
+  // when an earlier backward pass has overwritten the states the forward pass left),
+  // then step back through it
   char *lin = lam0, *lout = lam1;
+  const bool last_saved = tp.last_saved;
+  tp.last_saved = false;          // the recomputation below reuses the segment buffer
   for (long long sgm = nseg - 1; sgm >= 0; --sgm) {
     const int len = (int)std::min(K, T - sgm * K);
-    const bool last = sgm == nseg - 1;
+    const bool saved = sgm == nseg - 1 && last_saved;
     // state of step r of this segment: the natural checkpoint itself for r = 0
     auto at = [&](int r) -> char * {
-      return (natural && !last && r == 0) ? ck + ck_bytes * sgm : seg + state * r;
+      return (natural && !saved && r == 0) ? ck + ck_bytes * sgm : seg + state * r;
     };
-    if (!last) {
+    if (!saved) {
       if (natural) {
         for (int r = 0; r + 1 < len; ++r) {
-          set_step_factor(c, tck[sgm] + r);
+          set_step_factor(c, tp.tck[sgm] + r);
           ADJ_CUDA(launch_recompute_step(c->lattice, c->precision, c->a64, c->a32, aux_args(c),
                                          at(r), at(r + 1), st));
         }
       } else {
         ADJ_CUDA(load_raw(ck + ck_bytes * sgm));
-        c->t = tck[sgm];
-        if ((rc = step_saving(len)) != LBM_OK) { cleanup(); return rc; }
+        c->t = tp.tck[sgm];
+        const int rc = step_saving(len);
+        if (rc != LBM_OK) { adj_ws_free(c); return rc; }
       }
     }
     for (int r = len - 1; r >= 0; --r) {
-      set_step_factor(c, tck[sgm] + r);
+      set_step_factor(c, tp.tck[sgm] + r);
       ADJ_CUDA(launch_adjoint_step(c->lattice, c->precision, c->a64, c->a32, aux_args(c), dcoef,
                                    acc, at(r), lin, lout, gpart, st));
       std::swap(lin, lout);
@@ -1042,18 +1136,13 @@ int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *ma
   ADJ_CUDA(launch_adjoint_finish(c->lattice, gpart, pblocks, dgs, st));
   // back to the state after the forward run
   ADJ_CUDA(load_raw(fin));
-  c->t = t0 + T;
-  double hJ = 0.0;
+  c->t = tp.t0 + T;
   std::vector<double> hgs(19), htot(2 * nl);
-  ADJ_CUDA(cudaMemcpyAsync(&hJ, dJ, sizeof(double), cudaMemcpyDeviceToHost, st));
   ADJ_CUDA(cudaMemcpyAsync(hgs.data(), dgs, sizeof(double) * 19, cudaMemcpyDeviceToHost, st));
   if (nl)
     ADJ_CUDA(cudaMemcpyAsync(htot.data(), dtot, sizeof(double) * 2 * nl, cudaMemcpyDeviceToHost, st));
   ADJ_CUDA(cudaStreamSynchronize(st));
-  ok = true;
-  cleanup();
 #undef ADJ_CUDA
-  if (loss) *loss = hJ;
   if (grad_s)
     for (int k = 0; k < c->Q; ++k) grad_s[k] = with_lat(c->lattice, [&](auto lat) {
       using L = decltype(lat);
@@ -1082,7 +1171,36 @@ int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *ma
     }
     return 0;
   });
-  return check_status(c);
+  const int rc = check_status(c);
+  if (rc != LBM_OK) return rc;
+  // the state is the forward run's end state again: the tape stays usable
+  tp.serial = c->state_serial;
+  tp.valid = true;
+  return LBM_OK;
+}
+}  // namespace
+
+int lbm_adjoint_forward(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *mask,
+                        const double *u_target, double *loss) {
+  if (!c) return LBM_EINVAL;
+  DeviceGuard dg(c->device);
+  return adjoint_forward_impl(c, n_steps, checkpoint_every, mask, u_target, loss);
+}
+
+int lbm_adjoint_backward(lbm_ctx *c, double *grad_s, double *grad_q, double *grad_uw) {
+  if (!c) return LBM_EINVAL;
+  DeviceGuard dg(c->device);
+  return adjoint_backward_impl(c, grad_s, grad_q, grad_uw);
+}
+
+int lbm_adjoint(lbm_ctx *c, int n_steps, int checkpoint_every, const uint8_t *mask,
+                const double *u_target, double *loss, double *grad_s, double *grad_q,
+                double *grad_uw) {
+  if (!c) return LBM_EINVAL;
+  DeviceGuard dg(c->device);
+  int rc = adjoint_forward_impl(c, n_steps, checkpoint_every, mask, u_target, loss);
+  if (rc == LBM_OK) rc = adjoint_backward_impl(c, grad_s, grad_q, grad_uw);
+  return rc;
 }
 
 int lbm_query(const lbm_ctx *c, int *Q, int *D, int64_t *nodes, int64_t *fluid_nodes,
@@ -1267,7 +1385,10 @@ static int batch_run_plain(lbm_batch *b, int n) {
   for (int k = 0; k < n; ++k) {
     BCUDA(b, batch_launch(b, ((k & 1) != 0) != odd, false));
   }
-  for (lbm_ctx *c : b->ctx) c->t += n;
+  for (lbm_ctx *c : b->ctx) {
+    c->t += n;
+    c->state_serial += n;
+  }
   return LBM_OK;
 }
 
@@ -1295,7 +1416,7 @@ int lbm_batch_create(lbm_batch **out, int n, lbm_ctx *const *ctxs) {
   b->stream = ctxs[0]->stream;
   b->host_tiles.resize(n);
   b->versions.assign(n, -1);
-  cudaSetDevice(b->device);
+  DeviceGuard dg(b->device);
   const int rc = batch_refresh_if_needed(b);
   if (rc != LBM_OK) {
     g_create_error = b->err;
@@ -1308,7 +1429,7 @@ int lbm_batch_create(lbm_batch **out, int n, lbm_ctx *const *ctxs) {
 
 int lbm_batch_destroy(lbm_batch *b) {
   if (!b) return LBM_OK;
-  cudaSetDevice(b->device);
+  DeviceGuard dg(b->device);
   if (b->stream) cudaStreamSynchronize(b->stream);
   batch_drop_graph(b);
   cudaFree(b->inst);
@@ -1329,7 +1450,7 @@ int lbm_batch_set_config(lbm_batch *b, int order, int blocks_per_sm) {
   if (!b) return LBM_EINVAL;
   if (order < 0 || order > 2 || blocks_per_sm < 0 || blocks_per_sm > 32)
     return bfail(b, LBM_EINVAL, "lbm_batch_set_config: order in 0..2, blocks_per_sm in 0..32");
-  cudaSetDevice(b->device);
+  DeviceGuard dg(b->device);
   b->order = order;
   b->blocks_per_sm = blocks_per_sm;
   batch_drop_graph(b);
@@ -1339,7 +1460,7 @@ int lbm_batch_set_config(lbm_batch *b, int order, int blocks_per_sm) {
 int lbm_batch_step(lbm_batch *b, int n) {
   if (!b) return LBM_EINVAL;
   if (n < 0) return bfail(b, LBM_EINVAL, "lbm_batch_step: n < 0");
-  cudaSetDevice(b->device);
+  DeviceGuard dg(b->device);
   int rc = batch_refresh_if_needed(b);
   if (rc != LBM_OK) return rc;
   bool odd;
@@ -1380,7 +1501,10 @@ int lbm_batch_step(lbm_batch *b, int n) {
     b->graph_pairs = 1;
   }
   for (int k = 0; k + 1 < n; k += 2) BCUDA(b, cudaGraphLaunch(b->graph, b->stream));
-  for (lbm_ctx *c : b->ctx) c->t += n - (n & 1);
+  for (lbm_ctx *c : b->ctx) {
+    c->t += n - (n & 1);
+    c->state_serial += n - (n & 1);
+  }
   if (n & 1) return batch_run_plain(b, 1);
   return LBM_OK;
 }
@@ -1389,7 +1513,7 @@ int lbm_batch_tune(lbm_batch *b, int trial_steps, int *order_out, int *blocks_ou
   if (!b) return LBM_EINVAL;
   if (trial_steps < 2) return bfail(b, LBM_EINVAL, "lbm_batch_tune: trial_steps >= 2");
   trial_steps &= ~1;
-  cudaSetDevice(b->device);
+  DeviceGuard dg(b->device);
   int rc = batch_refresh_if_needed(b);
   if (rc != LBM_OK) return rc;
   bool odd;
