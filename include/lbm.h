@@ -286,19 +286,25 @@ int lbm_adjoint_backward(lbm_ctx *ctx, double *grad_s, double *grad_q, double *g
  * be at the same time parity when the batch steps.  Changes to a member context
  * (geometry, scheme, force) are picked up at the next batch call.
  * lbm_batch_set_config: order of tiles in the launch (0 context after context,
- * 1 round-robin over contexts, 2 largest context first) and resident blocks per SM
- * (0 = as many as fit).  lbm_batch_tune times every (order, blocks) pair over
- * trial_steps steps, keeps the fastest and restores the contexts' state, so tuning
- * does not advance the simulations. */
+ * 1 round-robin over contexts, 2 largest context first), resident blocks per SM
+ * (0 = as many as fit) and split: 1 (the default) gives every kernel class of
+ * members -- rows starting on 16-byte boundaries or not, skewed x-wrap or not --
+ * its own launch of the sweep specialised for it (aligned windows, no skew
+ * handling), all inside the same graph; 0 runs every member through the general
+ * sweep (unaligned windows, skew), one launch per step.  Grids whose slots need
+ * 64-bit indices always take the general sweep.  lbm_batch_tune times every
+ * (split, order, blocks) combination over trial_steps steps, keeps the fastest
+ * and restores the contexts' state, so tuning does not advance the simulations.
+ * lbm_batch_query also reports the kernel launches one step takes. */
 typedef struct lbm_batch lbm_batch;
 int lbm_batch_create(lbm_batch **out, int n, lbm_ctx *const *ctxs);
 int lbm_batch_destroy(lbm_batch *batch);
 int lbm_batch_set_stream(lbm_batch *batch, void *cuda_stream);
-int lbm_batch_set_config(lbm_batch *batch, int order, int blocks_per_sm);
-int lbm_batch_tune(lbm_batch *batch, int trial_steps, int *order, int *blocks_per_sm);
+int lbm_batch_set_config(lbm_batch *batch, int order, int blocks_per_sm, int split);
+int lbm_batch_tune(lbm_batch *batch, int trial_steps, int *order, int *blocks_per_sm, int *split);
 int lbm_batch_step(lbm_batch *batch, int n);
 int lbm_batch_query(const lbm_batch *batch, int *n_contexts, int64_t *tiles, int *order,
-                    int *blocks_per_sm);
+                    int *blocks_per_sm, int *launches_per_step);
 const char *lbm_batch_last_error(const lbm_batch *batch);
 
 /* The current device's FP64 fused multiply-add rate in GFLOP/s (an FMA counted as

@@ -27,11 +27,11 @@ cudaError_t launch_sweep_d3q15(int, bool, const SweepArgs<double> &, const Sweep
 int error_norms_noalloc(int device, int lattice, int precision, const AuxArgs &a, bool odd,
                         const double *u_ref, double *out, cudaStream_t st, const char **why);
 cudaError_t launch_sweep_batch_d2q9(int, bool, const void *, const TileDesc *, const int *, int,
-                                   bool, int, cudaStream_t, bool);
+                                   bool, bool, bool, int, cudaStream_t, bool);
 cudaError_t launch_sweep_batch_d3q19(int, bool, const void *, const TileDesc *, const int *, int,
-                                    bool, int, cudaStream_t, bool);
+                                    bool, bool, bool, int, cudaStream_t, bool);
 cudaError_t launch_sweep_batch_d3q15(int, bool, const void *, const TileDesc *, const int *, int,
-                                    bool, int, cudaStream_t, bool);
+                                    bool, bool, bool, int, cudaStream_t, bool);
 cudaError_t launch_sweep(int lattice, int precision, bool odd, const SweepArgs<double> &a64,
                          const SweepArgs<float> &a32, const TileDesc *tiles, int n_tiles, int bx,
                          cudaStream_t st) {
@@ -146,6 +146,11 @@ constexpr size_t kGuardBytes = 1024;
 
 static size_t pop_alloc_bytes(const lbm_ctx *c) {
   return (size_t)c->Q * slot_stride(c->N) * store_bytes(c->precision) + 2 * kPopPadBytes;
+}
+
+// bytes of the link buffer: one storage element per cut link
+static size_t link_bytes(const lbm_ctx *c) {
+  return (size_t)store_bytes(c->precision) * std::max<long long>(1, c->n_links);
 }
 
 template <class F>
@@ -619,8 +624,8 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *solid, int64_t n_links, const in
   CUDA_OR_FAIL(c, cudaMalloc((void **)&c->bmask, sizeof(uint32_t) * nb));
   CUDA_OR_FAIL(c, cudaMalloc((void **)&c->boff, sizeof(int32_t) * nb));
   CUDA_OR_FAIL(c, cudaMalloc(&c->coef, 4 * cb * std::max<long long>(1, n_links)));
-  CUDA_OR_FAIL(c, cudaMalloc(&c->lnk, (size_t)store_bytes(c->precision) * std::max<long long>(1, n_links)));
-  CUDA_OR_FAIL(c, cudaMemset(c->lnk, 0, (size_t)store_bytes(c->precision) * std::max<long long>(1, n_links)));
+  CUDA_OR_FAIL(c, cudaMalloc(&c->lnk, link_bytes(c)));
+  CUDA_OR_FAIL(c, cudaMemset(c->lnk, 0, link_bytes(c)));
   if (!bmask.empty()) {
     CUDA_OR_FAIL(c, cudaMemcpy(c->bmask, bmask.data(), sizeof(uint32_t) * bmask.size(),
                                cudaMemcpyHostToDevice));
@@ -932,7 +937,7 @@ int adjoint_forward_impl(lbm_ctx *c, int n_steps, int checkpoint_every, const ui
   const size_t csize = c->precision == LBM_F64 ? sizeof(double) : sizeof(float);
   const size_t state = (size_t)c->Q * c->N * csize;               // natural layout, compute type
   const size_t raw_pop = pop_alloc_bytes(c);
-  const size_t raw_lnk = (size_t)store_bytes(c->precision) * std::max<long long>(1, c->n_links);
+  const size_t raw_lnk = link_bytes(c);
   const long long nl1 = std::max<long long>(1, c->n_links);
   const bool natural = c->precision == LBM_F64 || c->precision == LBM_F32_DEV;
   const size_t ck_bytes = natural ? state : raw_pop + raw_lnk;
@@ -1036,7 +1041,7 @@ int adjoint_backward_impl(lbm_ctx *c, double *grad_s, double *grad_q, double *gr
   const size_t csize = c->precision == LBM_F64 ? sizeof(double) : sizeof(float);
   const size_t state = (size_t)c->Q * c->N * csize;
   const size_t raw_pop = pop_alloc_bytes(c);
-  const size_t raw_lnk = (size_t)store_bytes(c->precision) * std::max<long long>(1, c->n_links);
+  const size_t raw_lnk = link_bytes(c);
   const long long nl = c->n_links;
   const long long nl1 = std::max<long long>(1, nl);
   const bool natural = c->precision == LBM_F64 || c->precision == LBM_F32_DEV;
@@ -1224,6 +1229,16 @@ const char *lbm_last_error(const lbm_ctx *c) {
 // Batches: many contexts advanced by one persistent launch per step, replayed
 // from a CUDA graph.
 // ---------------------------------------------------------------------------
+// kernel classes of batch members: 2 * (rows aligned) + (skewed wrap); the general
+// class (unaligned, skewed) serves every member
+constexpr int kBatchClasses = 4;
+constexpr int kBatchGeneral = 1;
+struct BatchList {
+  TileDesc *tiles = nullptr;
+  int *tile_inst = nullptr;
+  int n = 0;
+};
+
 struct lbm_batch {
   std::vector<lbm_ctx *> ctx;
   int lattice = 0, precision = 0, device = 0;
@@ -1231,9 +1246,9 @@ struct lbm_batch {
   std::vector<std::vector<TileDesc>> host_tiles;   // per context
   std::vector<long long> versions;
   void *inst = nullptr;          // SweepArgs per context (compute type of the precision)
-  TileDesc *tiles = nullptr;
-  int *tile_inst = nullptr;
+  BatchList lists[kBatchClasses];  // tile lists per kernel class (batch_upload)
   int n_tiles = 0;
+  bool split = true;             // one launch per kernel class (lbm_batch_set_config)
   bool big = false;
   int order = 1;                 // 0 context-major, 1 round-robin, 2 largest context first
   int blocks_per_sm = 0;         // 0: as many as fit
@@ -1268,51 +1283,68 @@ static void batch_drop_graph(lbm_batch *b) {
   b->graph_pairs = 0;
 }
 
-// merged tile list in the batch's order and the per-context argument table
+// Tile lists of the batch, one per kernel class, each in the batch's order.  A
+// member's class is (rows start on 16-byte boundaries, skewed x-wrap); with the
+// split on, each class runs the sweep specialised for it (aligned windows, no
+// skew handling), otherwise -- and for grids whose slots need 64-bit indices --
+// every member goes through the general kernel (unaligned windows, skew).
+static bool member_aligned(const lbm_ctx *c) {
+  return ((long long)c->nx * store_bytes(c->precision)) % 16 == 0;
+}
 static int batch_upload(lbm_batch *b) {
   const int n = (int)b->ctx.size();
-  std::vector<TileDesc> t;
-  std::vector<int> ti;
-  size_t total = 0;
-  for (auto &v : b->host_tiles) total += v.size();
-  t.reserve(total);
-  ti.reserve(total);
+  b->big = false;
+  for (lbm_ctx *c : b->ctx)
+    if ((long long)c->Q * slot_stride(c->N) >= (1LL << 31)) b->big = true;
+  std::vector<int> cls_of(n, kBatchGeneral);
+  if (b->split && !b->big)
+    for (int k = 0; k < n; ++k) {
+      const lbm_ctx *c = b->ctx[k];
+      cls_of[k] = (member_aligned(c) ? 2 : 0) + ((c->sy != 0 || c->sz != 0) ? 1 : 0);
+    }
   std::vector<int> ctx_order(n);
   for (int k = 0; k < n; ++k) ctx_order[k] = k;
   if (b->order == 2)
     std::stable_sort(ctx_order.begin(), ctx_order.end(), [&](int p, int q) {
       return b->host_tiles[p].size() > b->host_tiles[q].size();
     });
-  if (b->order == 1) {
-    // round-robin: one tile of every context in turn
-    std::vector<size_t> pos(n, 0);
-    bool more = true;
-    while (more) {
-      more = false;
-      for (int k : ctx_order)
-        if (pos[k] < b->host_tiles[k].size()) {
-          t.push_back(b->host_tiles[k][pos[k]++]);
-          ti.push_back(k);
-          more = true;
-        }
-    }
-  } else {
-    for (int k : ctx_order)
-      for (const TileDesc &d : b->host_tiles[k]) {
-        t.push_back(d);
-        ti.push_back(k);
+  b->n_tiles = 0;
+  for (int cl = 0; cl < kBatchClasses; ++cl) {
+    BatchList &bl = b->lists[cl];
+    std::vector<TileDesc> t;
+    std::vector<int> ti;
+    if (b->order == 1) {
+      // round-robin: one tile of every member of the class in turn
+      std::vector<size_t> pos(n, 0);
+      bool more = true;
+      while (more) {
+        more = false;
+        for (int k : ctx_order)
+          if (cls_of[k] == cl && pos[k] < b->host_tiles[k].size()) {
+            t.push_back(b->host_tiles[k][pos[k]++]);
+            ti.push_back(k);
+            more = true;
+          }
       }
-  }
-  b->n_tiles = (int)t.size();
-  cudaFree(b->tiles);
-  cudaFree(b->tile_inst);
-  b->tiles = nullptr;
-  b->tile_inst = nullptr;
-  BCUDA(b, cudaMalloc((void **)&b->tiles, sizeof(TileDesc) * std::max<size_t>(1, t.size())));
-  BCUDA(b, cudaMalloc((void **)&b->tile_inst, sizeof(int) * std::max<size_t>(1, ti.size())));
-  if (!t.empty()) {
-    BCUDA(b, cudaMemcpy(b->tiles, t.data(), sizeof(TileDesc) * t.size(), cudaMemcpyHostToDevice));
-    BCUDA(b, cudaMemcpy(b->tile_inst, ti.data(), sizeof(int) * ti.size(), cudaMemcpyHostToDevice));
+    } else {
+      for (int k : ctx_order)
+        if (cls_of[k] == cl)
+          for (const TileDesc &d : b->host_tiles[k]) {
+            t.push_back(d);
+            ti.push_back(k);
+          }
+    }
+    cudaFree(bl.tiles);
+    cudaFree(bl.tile_inst);
+    bl.tiles = nullptr;
+    bl.tile_inst = nullptr;
+    bl.n = (int)t.size();
+    b->n_tiles += bl.n;
+    if (t.empty()) continue;
+    BCUDA(b, cudaMalloc((void **)&bl.tiles, sizeof(TileDesc) * t.size()));
+    BCUDA(b, cudaMalloc((void **)&bl.tile_inst, sizeof(int) * ti.size()));
+    BCUDA(b, cudaMemcpy(bl.tiles, t.data(), sizeof(TileDesc) * t.size(), cudaMemcpyHostToDevice));
+    BCUDA(b, cudaMemcpy(bl.tile_inst, ti.data(), sizeof(int) * ti.size(), cudaMemcpyHostToDevice));
   }
   return LBM_OK;
 }
@@ -1322,11 +1354,9 @@ static int batch_upload_args(lbm_batch *b) {
   const bool f64 = b->precision == LBM_F64;
   const size_t one = f64 ? sizeof(SweepArgs<double>) : sizeof(SweepArgs<float>);
   std::vector<unsigned char> h(one * n);
-  b->big = false;
   for (int k = 0; k < n; ++k) {
     lbm_ctx *c = b->ctx[k];
     std::memcpy(h.data() + one * k, f64 ? (const void *)&c->a64 : (const void *)&c->a32, one);
-    if ((long long)c->Q * slot_stride(c->N) >= (1LL << 31)) b->big = true;
     b->versions[k] = c->version;
   }
   if (!b->inst) BCUDA(b, cudaMalloc(&b->inst, one * n));
@@ -1353,17 +1383,27 @@ static int batch_refresh_if_needed(lbm_batch *b) {
 }
 
 static cudaError_t batch_launch(lbm_batch *b, bool odd, bool prepare_only) {
-  switch (b->lattice) {
-    case LBM_D2Q9:
-      return launch_sweep_batch_d2q9(b->precision, odd, b->inst, b->tiles, b->tile_inst, b->n_tiles,
-                                     b->big, b->blocks_per_sm, b->stream, prepare_only);
-    case LBM_D3Q15:
-      return launch_sweep_batch_d3q15(b->precision, odd, b->inst, b->tiles, b->tile_inst, b->n_tiles,
-                                      b->big, b->blocks_per_sm, b->stream, prepare_only);
-    default:
-      return launch_sweep_batch_d3q19(b->precision, odd, b->inst, b->tiles, b->tile_inst, b->n_tiles,
-                                      b->big, b->blocks_per_sm, b->stream, prepare_only);
+  for (int cl = 0; cl < kBatchClasses; ++cl) {
+    const BatchList &bl = b->lists[cl];
+    if (bl.n == 0) continue;
+    const bool aligned = (cl & 2) != 0, skew = (cl & 1) != 0;
+    cudaError_t e;
+    switch (b->lattice) {
+      case LBM_D2Q9:
+        e = launch_sweep_batch_d2q9(b->precision, odd, b->inst, bl.tiles, bl.tile_inst, bl.n, b->big,
+                                    aligned, skew, b->blocks_per_sm, b->stream, prepare_only);
+        break;
+      case LBM_D3Q15:
+        e = launch_sweep_batch_d3q15(b->precision, odd, b->inst, bl.tiles, bl.tile_inst, bl.n, b->big,
+                                     aligned, skew, b->blocks_per_sm, b->stream, prepare_only);
+        break;
+      default:
+        e = launch_sweep_batch_d3q19(b->precision, odd, b->inst, bl.tiles, bl.tile_inst, bl.n, b->big,
+                                     aligned, skew, b->blocks_per_sm, b->stream, prepare_only);
+    }
+    if (e != cudaSuccess) return e;
   }
+  return cudaSuccess;
 }
 
 static int batch_check_parity(lbm_batch *b, bool *odd) {
@@ -1433,8 +1473,10 @@ int lbm_batch_destroy(lbm_batch *b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   batch_drop_graph(b);
   cudaFree(b->inst);
-  cudaFree(b->tiles);
-  cudaFree(b->tile_inst);
+  for (BatchList &bl : b->lists) {
+    cudaFree(bl.tiles);
+    cudaFree(bl.tile_inst);
+  }
   delete b;
   return LBM_OK;
 }
@@ -1446,13 +1488,15 @@ int lbm_batch_set_stream(lbm_batch *b, void *stream) {
   return LBM_OK;
 }
 
-int lbm_batch_set_config(lbm_batch *b, int order, int blocks_per_sm) {
+int lbm_batch_set_config(lbm_batch *b, int order, int blocks_per_sm, int split) {
   if (!b) return LBM_EINVAL;
-  if (order < 0 || order > 2 || blocks_per_sm < 0 || blocks_per_sm > 32)
-    return bfail(b, LBM_EINVAL, "lbm_batch_set_config: order in 0..2, blocks_per_sm in 0..32");
+  if (order < 0 || order > 2 || blocks_per_sm < 0 || blocks_per_sm > 32 || split < 0 || split > 1)
+    return bfail(b, LBM_EINVAL,
+                 "lbm_batch_set_config: order in 0..2, blocks_per_sm in 0..32, split 0 or 1");
   DeviceGuard dg(b->device);
   b->order = order;
   b->blocks_per_sm = blocks_per_sm;
+  b->split = split != 0;
   batch_drop_graph(b);
   return batch_upload(b);
 }
@@ -1509,7 +1553,7 @@ int lbm_batch_step(lbm_batch *b, int n) {
   return LBM_OK;
 }
 
-int lbm_batch_tune(lbm_batch *b, int trial_steps, int *order_out, int *blocks_out) {
+int lbm_batch_tune(lbm_batch *b, int trial_steps, int *order_out, int *blocks_out, int *split_out) {
   if (!b) return LBM_EINVAL;
   if (trial_steps < 2) return bfail(b, LBM_EINVAL, "lbm_batch_tune: trial_steps >= 2");
   trial_steps &= ~1;
@@ -1521,14 +1565,14 @@ int lbm_batch_tune(lbm_batch *b, int trial_steps, int *order_out, int *blocks_ou
   // snapshot populations and link buffers: tuning leaves the state untouched
   size_t bytes = 0;
   for (lbm_ctx *c : b->ctx)
-    bytes += pop_alloc_bytes(c) + (size_t)store_bytes(c->precision) * std::max<long long>(1, c->n_links);
+    bytes += pop_alloc_bytes(c) + link_bytes(c);
   void *snap = nullptr;
   BCUDA(b, cudaMalloc(&snap, bytes));
   auto copy_state = [&](bool save) -> cudaError_t {
     size_t o = 0;
     for (lbm_ctx *c : b->ctx) {
       const size_t pb = pop_alloc_bytes(c);
-      const size_t lb = (size_t)store_bytes(c->precision) * std::max<long long>(1, c->n_links);
+      const size_t lb = link_bytes(c);
       char *s = static_cast<char *>(snap) + o;
       cudaError_t e = save ? cudaMemcpyAsync(s, c->pop_alloc, pb, cudaMemcpyDeviceToDevice, b->stream)
                            : cudaMemcpyAsync(c->pop_alloc, s, pb, cudaMemcpyDeviceToDevice, b->stream);
@@ -1550,8 +1594,11 @@ int lbm_batch_tune(lbm_batch *b, int trial_steps, int *order_out, int *blocks_ou
   const int blocks[3] = {0, 4, 3};
   float best = 1e30f;
   int best_o = b->order, best_b = b->blocks_per_sm;
+  bool best_s = b->split;
+  for (int si = 0; si < 2 && e == cudaSuccess && rc == LBM_OK; ++si)
   for (int oi = 0; oi < 3 && e == cudaSuccess; ++oi)
     for (int bi = 0; bi < 3 && e == cudaSuccess; ++bi) {
+      b->split = si == 0;
       b->order = orders[oi];
       b->blocks_per_sm = blocks[bi];
       if ((rc = batch_upload(b)) != LBM_OK) break;
@@ -1566,6 +1613,7 @@ int lbm_batch_tune(lbm_batch *b, int trial_steps, int *order_out, int *blocks_ou
         best = ms;
         best_o = orders[oi];
         best_b = blocks[bi];
+        best_s = b->split;
       }
       if (e == cudaSuccess) e = copy_state(false);
     }
@@ -1577,20 +1625,27 @@ int lbm_batch_tune(lbm_batch *b, int trial_steps, int *order_out, int *blocks_ou
   if (e != cudaSuccess) return bfail(b, LBM_ECUDA, "lbm_batch_tune: %s", cudaGetErrorString(e));
   b->order = best_o;
   b->blocks_per_sm = best_b;
+  b->split = best_s;
   batch_drop_graph(b);
   if ((rc = batch_upload(b)) != LBM_OK) return rc;
   if (order_out) *order_out = best_o;
   if (blocks_out) *blocks_out = best_b;
+  if (split_out) *split_out = best_s ? 1 : 0;
   return LBM_OK;
 }
 
 int lbm_batch_query(const lbm_batch *b, int *n_contexts, int64_t *tiles, int *order,
-                    int *blocks_per_sm) {
+                    int *blocks_per_sm, int *launches_per_step) {
   if (!b) return LBM_EINVAL;
   if (n_contexts) *n_contexts = (int)b->ctx.size();
   if (tiles) *tiles = b->n_tiles;
   if (order) *order = b->order;
   if (blocks_per_sm) *blocks_per_sm = b->blocks_per_sm;
+  if (launches_per_step) {
+    int k = 0;
+    for (const BatchList &bl : b->lists) k += bl.n > 0 ? 1 : 0;
+    *launches_per_step = k;
+  }
   return LBM_OK;
 }
 

@@ -793,26 +793,39 @@ cudaError_t launch_sweep_t(bool odd, const SweepArgs<typename Storage<T>::C> &a,
   return cudaGetLastError();
 }
 
-// One step of a batch: the tiles of all instances in one persistent launch, each
-// tile reading its instance's arguments from the table.  Instances may differ in
-// size, alignment and skew; the unaligned-window path serves all of them.
-// prepare_only: set up the kernels' launch attributes without launching (done once
-// before a stream capture).
+// One step of a batch: the tiles of one kernel class of members in one persistent
+// launch, each tile reading its member's arguments from the table.  aligned: every
+// member's rows start on 16-byte boundaries (aligned-window path); skew: some
+// member has a skewed x-wrap.  Batches whose slots need 64-bit indices (big) use
+// the general kernel (unaligned windows, skew) for every member.  prepare_only:
+// set up the kernel's launch attributes without launching (done once before a
+// stream capture).
 template <class L, class T>
 cudaError_t launch_sweep_batch_t(bool odd, const SweepArgs<typename Storage<T>::C> *inst,
                                  const TileDesc *tiles, const int *tile_inst, int n_tiles,
-                                 bool big, int blocks_per_sm, cudaStream_t st, bool prepare_only) {
+                                 bool big, bool aligned, bool skew, int blocks_per_sm, cudaStream_t st,
+                                 bool prepare_only) {
   if (n_tiles == 0) return cudaSuccess;
   using A = SweepArgs<typename Storage<T>::C>;
   const size_t smem = kWarpsPerBlock * warp_smem_bytes<L, T>();
   A dummy{};
   dummy.wait_polls = kWaitLimit;
-#define LBM_LAUNCH_B(O, I)                                                                       \
-  launch_persistent<sweep_kernel<L, T, O, true, false, I, true>>(dummy, tiles, n_tiles, smem, st, \
-                                                                 inst, tile_inst, blocks_per_sm, \
-                                                                 prepare_only)
-  if (big) { if (odd) LBM_LAUNCH_B(true, long long); else LBM_LAUNCH_B(false, long long); }
-  else { if (odd) LBM_LAUNCH_B(true, int); else LBM_LAUNCH_B(false, int); }
+#define LBM_LAUNCH_B(O, S, AL, I)                                                                  \
+  launch_persistent<sweep_kernel<L, T, O, S, AL, I, true>>(dummy, tiles, n_tiles, smem, st, inst,  \
+                                                           tile_inst, blocks_per_sm, prepare_only)
+  if (big) {
+    if (odd) LBM_LAUNCH_B(true, true, false, long long);
+    else LBM_LAUNCH_B(false, false, false, long long);
+  } else if (!odd) {
+    if (aligned) LBM_LAUNCH_B(false, false, true, int);
+    else LBM_LAUNCH_B(false, false, false, int);
+  } else if (aligned) {
+    if (skew) LBM_LAUNCH_B(true, true, true, int);
+    else LBM_LAUNCH_B(true, false, true, int);
+  } else {
+    if (skew) LBM_LAUNCH_B(true, true, false, int);
+    else LBM_LAUNCH_B(true, false, false, int);
+  }
 #undef LBM_LAUNCH_B
   return cudaGetLastError();
 }

@@ -59,15 +59,22 @@ def test_batch_equals_individual_steps(prec, steps):
 
 
 @pytest.mark.parametrize("order", [0, 1, 2])
-def test_batch_orders_and_graph_replay(order):
+@pytest.mark.parametrize("split", [0, 1])
+def test_batch_orders_and_graph_replay(order, split):
+    """Every tile order, with the members split into kernel classes (one launch per
+    class: members whose rows start on 16-byte boundaries take the aligned-window
+    sweep) or all through the general sweep; the graph is replayed."""
     torch = require_gpu()
     stream = torch.cuda.current_stream().cuda_stream
     ws = _members(5, seed=4)
+    aligned = [w["shape"][0] % 4 == 0 for w in ws]
+    assert any(aligned) and not all(aligned)       # both classes present
     solo = _make(ws, "f32", stream)
     grouped = _make(ws, "f32", stream)
     batch = B.Batch(grouped)
     batch.set_stream(stream)
-    batch.set_config(order, 3)
+    batch.set_config(order, 3, split)
+    assert batch.query()["launches_per_step"] == (2 if split else 1)
     for rep in range(3):            # the graph is captured once and replayed
         batch.step(10)
         for s in solo:
@@ -88,8 +95,8 @@ def test_tune_leaves_state_unchanged():
     before = [s.get_populations() for s in sims]
     batch = B.Batch(sims)
     batch.set_stream(stream)
-    order, blocks = batch.tune(6)
-    assert order in (0, 1, 2) and blocks in (0, 3, 4)
+    order, blocks, split = batch.tune(6)
+    assert order in (0, 1, 2) and blocks in (0, 3, 4) and split in (0, 1)
     q = batch.query()
     assert q["order"] == order and q["blocks_per_sm"] == blocks and q["contexts"] == 4
     for s, f0, w in zip(sims, before, ws):
