@@ -52,6 +52,7 @@ WORKLOAD = ("D3Q19 MRT body-force Poiseuille flow in a tilted periodic pipe, L=2
 SCHEME = (0.0, 1.0, 0.0, 1.0)
 BYTES = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}
 PROFILE = os.path.join(ROOT, "profiles", "sweep_d3q19_f32_pipe192.txt")
+PROFILE_F64 = os.path.join(ROOT, "profiles", "sweep_d3q19_f64_ops_pipe128.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1712_08288_gb300", "csrc", f)
                   for f in ("sweep.cuh", "common.cuh", "lattice.h", "lbm_internal.h")]
 
@@ -64,13 +65,13 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the FP32 sweep from the committed ncu summary, or
-    None when the summary is absent or the kernel source changed since."""
-    if not os.path.exists(PROFILE):
+def _profile_field(path, key):
+    """A figure from a committed ncu summary (key: value lines), or None when the
+    summary is absent or the kernel source changed since it was taken."""
+    if not os.path.exists(path):
         return None
     vals = {}
-    with open(PROFILE) as fh:
+    with open(path) as fh:
         for line in fh:
             if ":" in line:
                 k, v = line.split(":", 1)
@@ -78,9 +79,20 @@ def profiled_traffic():
     if vals.get("kernel_source_sha256_16") != kernel_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_launch_full_size"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the FP32 sweep at the bench's size (ncu summary)."""
+    return _profile_field(PROFILE, "dram_bytes_per_launch_full_size")
+
+
+def profiled_fp64_flops():
+    """FP64 operations per fluid-node update of the FP64 sweep (ncu: DADD + DMUL +
+    2 DFMA thread instructions per launch over the fluid nodes)."""
+    return _profile_field(PROFILE_F64, "fp64_flops_per_fluid_node")
 
 
 def peaks():
@@ -184,8 +196,9 @@ def build_sim(w, precision, torch, stream):
 
 def time_steps(sim, torch, stream, steps, warmup, per_launch=True):
     """Warm-up, then K single-sweep launches bracketed by events; returns
-    (total ms, list of per-launch ms)."""
-    sim.step(warmup)
+    (total ms, list of per-launch ms).  The warm-up count is rounded up to an even
+    number, so that the first timed launch is an even step."""
+    sim.step(warmup + (warmup & 1))
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)] if per_launch else []
@@ -243,15 +256,41 @@ def run_gpu(args):
     status32 = sim.error_norms(None, check=False)["status"]
     del sim
 
-    # ---- FP64 storage on the same workload -----------------------------------
-    sim = build_sim(w, "f64", torch, stream)
-    sim.init_equilibrium(None, np.nan_to_num(w["u_exact"]))
-    k64 = max(10, args.steps // 8)
-    total64, launches64 = time_steps(sim, torch, stream, k64, min(args.warmup, 5))
-    mlups64 = n_fluid * k64 / (total64 * 1e-3) / 1e6
-    l64 = float(np.mean(launches64))
-    ach64 = 2 * Q * BYTES["f64"] * n_fluid / (l64 * 1e-3) / 1e9
-    del sim
+    # ---- the other storage precisions on the same workload ---------------------
+    prec_lines = {"f32": {"even_us": round(float(np.mean(launches[0::2])) * 1e3, 1),
+                          "odd_us": round(float(np.mean(launches[1::2])) * 1e3, 1),
+                          "mlups": round(mlups, 1), "frac_of_hbm": round(achieved / hbm, 4)}}
+    fp64_peak = None
+    for prec in ("f64", "bf16", "f16"):
+        sim = build_sim(w, prec, torch, stream)
+        sim.init_equilibrium(None, np.nan_to_num(w["u_exact"]))
+        kp = max(10, args.steps // 8) if prec == "f64" else max(20, args.steps // 2)
+        kp += kp & 1                                   # even and odd steps alike
+        tot_p, ls_p = time_steps(sim, torch, stream, kp, min(args.warmup, 5))
+        lm = float(np.mean(ls_p))
+        gbs = 2 * Q * BYTES[prec] * n_fluid / (lm * 1e-3) / 1e9
+        line_p = {"mlups": round(n_fluid * kp / (tot_p * 1e-3) / 1e6, 1), "steps": kp,
+                  "even_us": round(float(np.mean(ls_p[0::2])) * 1e3, 1),
+                  "odd_us": round(float(np.mean(ls_p[1::2])) * 1e3, 1),
+                  "bytes_per_node": 2 * Q * BYTES[prec], "achieved_GBs": round(gbs, 1),
+                  "frac_of_hbm": round(gbs / hbm, 4)}
+        if prec == "f64":
+            # the FP64 sweep is bound by the FP64 pipe on this GPU: report it against
+            # the measured FMA rate, with the FP64 operations per fluid node counted
+            # by ncu on the same kernel (profiles/)
+            from paper_1712_08288_gb300 import binding as B
+            fp64_peak = B.probe_fp64_rate()
+            fl_per_node = profiled_fp64_flops()
+            line_p["fp64_peak_gflops"] = round(fp64_peak, 1)
+            if fl_per_node:
+                ach_fl = fl_per_node * n_fluid / (lm * 1e-3) / 1e9
+                line_p["roofline"] = {"bound": "fp64", "flops_per_node": fl_per_node,
+                                      "achieved_gflops": round(ach_fl, 1),
+                                      "frac_of_fp64_peak": round(ach_fl / fp64_peak, 4)}
+        prec_lines[prec] = line_p
+        del sim
+    mlups64 = prec_lines["f64"]["mlups"]
+    k64 = prec_lines["f64"]["steps"]
 
     # ---- D3Q15 (the paper's own 3D lattice) on the same workload --------------
     d15 = None
@@ -289,21 +328,10 @@ def run_gpu(args):
            "note": "one job: initial field H2D, K sweeps, rho and u D2H; bytes per sweep"}
     del sim
 
-    # ---- accuracy: FP32 vs FP64 against the analytic profile (untimed) --------
+    # ---- accuracy: every precision against the analytic profile (untimed) ------
     acc = None
     if args.accuracy_steps > 0 and rank == 0:
-        acc = {}
-        wa = W.tilted_pipe_3d(args.accuracy_L)
-        for prec in ("f32", "f64"):
-            s2 = build_sim(wa, prec, torch, stream)
-            s2.init_equilibrium(None, np.nan_to_num(wa["u_exact"]))
-            s2.step(args.accuracy_steps)
-            nrm = s2.error_norms(np.nan_to_num(wa["u_exact"]), check=False)
-            acc[prec] = {"E_r": nrm["l2_rel"], "linf": nrm["linf"]}
-            del s2
-        acc["L"] = args.accuracy_L
-        acc["steps"] = args.accuracy_steps
-        acc["matched"] = abs(acc["f32"]["E_r"] - acc["f64"]["E_r"]) <= 0.1 * acc["f64"]["E_r"]
+        acc = run_accuracy(args, torch, stream)
 
     # ---- ensemble: batched persistent graph launch vs one launch per instance --
     ens = None
@@ -345,10 +373,7 @@ def run_gpu(args):
                          "traffic": traffic, "kernel": "sweep_kernel<D3Q19,float>",
                          "algorithmic_bytes_per_launch": alg_bytes,
                          "launch_ms": launch_ms},
-            "fp64": {"value": round(mlups64, 1), "unit": "MLUPS", "steps": k64,
-                     "launch_ms": l64, "achieved_GBs": round(ach64, 1),
-                     "frac_of_hbm": round(ach64 / hbm, 4),
-                     "note": "FP64 storage and arithmetic, same workload"},
+            "precisions": prec_lines,
             "d3q15": d15,
             "accuracy": acc,
             "ensemble": ens,
@@ -361,10 +386,82 @@ def run_gpu(args):
             "cpu_baseline": cpu,
             "status_f32": status32,
         }
+        line["summary"] = summary(line)      # last: the compact digest ends the line
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def summary(line):
+    """A compact digest of the sections (roofline fractions per precision, errors
+    and orders, adjoint and ensemble figures), placed at the end of the line."""
+    def g(d, *keys):
+        for k in keys:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return d
+
+    def r(v, n=4):
+        return None if v is None else (round(v, n) if isinstance(v, float) else v)
+    pr = line.get("precisions") or {}
+    out = {"frac_hbm": {p: g(pr, p, "frac_of_hbm") for p in ("f32", "bf16", "f16", "f64")},
+           "mlups": {p: g(pr, p, "mlups") for p in ("f32", "bf16", "f16", "f64")},
+           "f64_frac_of_fp64_peak": g(pr, "f64", "roofline", "frac_of_fp64_peak")}
+    acc = line.get("accuracy")
+    if acc:
+        out["pipe_E_r"] = {"L": acc["L"], **{p: ["%.4g" % v for v in acc[p]] for p in ("f64", "f32", "bf16", "f16")}}
+        out["pipe_order"] = {p: r(acc.get("order_" + p), 3) for p in ("f64", "f32", "bf16", "f16")}
+    ref = line.get("refinement")
+    if ref:
+        out["couette_order"] = {"f64": r(ref.get("order_f64"), 3), "f32": r(ref.get("order_f32"), 3),
+                                "sizes": ref.get("sizes")}
+    tg = line.get("taylor_green")
+    if tg:
+        out["tg_order"] = {k: r(v.get("order"), 3) for k, v in tg.items() if isinstance(v, dict)}
+    adj = line.get("adjoint")
+    if adj:
+        out["adjoint"] = {"bwd_over_fwd_f32": g(adj, "f32", "backward_over_forward"),
+                          "fwd_over_step_f32": g(adj, "f32", "forward_over_lbm_step"),
+                          "fd_rel_f64": r(g(adj, "f64", "rel_err_vs_fd"), 10)}
+    ens = line.get("ensemble")
+    if ens:
+        out["ensemble"] = {"mlups": ens.get("batched_graph_mlups"), "frac_hbm": ens.get("frac_of_hbm"),
+                           "speedup": ens.get("speedup")}
+    return out
+
+
+def run_accuracy(args, torch, stream):
+    """The D3Q19 tilted pipe at L = 64, 128, 256 from the analytic-equilibrium start,
+    args.accuracy_steps steps in every storage precision: E_r against the analytic
+    Hagen-Poiseuille parabola, the least-squares order over L per precision, and
+    which precisions match FP64's error (within 10 %, the metric's matched-error
+    rule) at each size."""
+    from paper_1712_08288_gb300 import workloads as W
+    sizes = [int(v) for v in args.accuracy_sizes.split(",") if v]
+    precs = ("f64", "f32", "bf16", "f16")
+    out = {"workload": "D3Q19 tilted pipe, analytic start, %d steps" % args.accuracy_steps,
+           "L": sizes, "steps": args.accuracy_steps}
+    t_start = time.perf_counter()
+    for prec in precs:
+        out[prec] = []
+    for L in sizes:
+        wa = W.tilted_pipe_3d(L)
+        ue = np.nan_to_num(wa["u_exact"])
+        for prec in precs:
+            s2 = build_sim(wa, prec, torch, stream)
+            s2.init_equilibrium(None, ue)
+            s2.step(args.accuracy_steps)
+            out[prec].append(s2.error_norms(ue, check=False)["l2_rel"])
+            del s2
+    for prec in precs:
+        e = out[prec]
+        out["order_" + prec] = (float(-np.polyfit(np.log(sizes), np.log(e), 1)[0])
+                                if len(sizes) > 1 else None)
+        out["matched_" + prec] = [bool(abs(a - b) <= 0.1 * b) for a, b in zip(e, out["f64"])]
+    out["seconds"] = round(time.perf_counter() - t_start, 1)
+    return out
 
 
 def run_ensemble(args, torch, stream):
@@ -406,7 +503,7 @@ def run_ensemble(args, torch, stream):
     sims = fresh()
     batch = B.Batch(sims)
     batch.set_stream(stream.cuda_stream)
-    order, blocks = batch.tune(20)
+    order, blocks, split = batch.tune(20)
     batch.step(4)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -422,17 +519,25 @@ def run_ensemble(args, torch, stream):
             "one_launch_per_instance_mlups": round(nf * K / (ms_single * 1e-3) / 1e6, 1),
             "speedup": round(ms_single / ms_batch, 2),
             "alg_GBs": round(2 * 9 * 4 * nf * K / (ms_batch * 1e-3) / 1e9, 1),
-            "tuned": {"order": B.Batch.ORDERS[order], "blocks_per_sm": blocks, "tiles": q["tiles"]},
+            "frac_of_hbm": round(2 * 9 * 4 * nf * K / (ms_batch * 1e-3) / 1e9 / peaks()[0], 4),
+            "tuned": {"order": B.Batch.ORDERS[order], "blocks_per_sm": blocks, "split_by_class": bool(split),
+                      "launches_per_step": q["launches_per_step"], "tiles": q["tiles"]},
             "workload": "D2Q9 circular Couette ensemble, seed 0, n ~ U{48..768}, FP32 deviations"}
 
 
 def run_refinement(args, torch, stream):
-    """Grid refinement of the circular Couette problem (D2Q9, curved walls, 64^2
-    configuration scaled by n/64 with diffusive scaling): each n runs in FP64 from
-    the analytic-equilibrium start until the relative change of u over 200 steps is
-    below 1e-10, then FP32 deviation storage runs the same number of steps; E_r
-    against the analytic profile and the least-squares order of both.  Throughput
-    at n = 2048 is timed separately (a fixed number of steps, not to steady state)."""
+    """Grid refinement of the circular Couette problem (D2Q9, curved walls, the 64^2
+    configuration scaled by n/64 in diffusive scaling) to a steady state.
+
+    Each n first runs with FP32 deviation storage from the analytic-equilibrium
+    start for ten diffusion times tau = (R2 - R1)^2 / (pi^2 nu) (the slowest decay
+    time of the annulus), which leaves the start's transient below FP32's own
+    rounding; its E_r and residual are the FP32 result.  FP64 storage then starts
+    from the FP32 end state (all populations copied) and steps until the relative
+    change of u over 200 steps is below 1e-10; its E_r is the FP64 result.  A
+    steady state does not depend on the start, and the FP32 run only removes most
+    of the O(tau) spin-up from the FP64 run.  Orders by least squares of log E_r
+    against log n; throughput at n = 2048 is timed separately (fixed step counts)."""
     from paper_1712_08288_gb300 import workloads as W
     sizes = [n for n in (32, 64, 128, 256, 512, 1024, 2048) if n <= args.refine_max]
     chunk, tol = 200, 1e-10
@@ -441,29 +546,40 @@ def run_refinement(args, torch, stream):
     for n in sizes:
         w = W.couette_config(n)
         ue = np.nan_to_num(w["u_exact"])
-        sim = build_sim(w, "f64", torch, stream)
-        sim.init_equilibrium(None, ue)
-        sim.error_norms(ue, check=False)
-        steps, res = 0, 1.0
-        while res >= tol and steps < args.refine_max_steps:
-            sim.step(chunk)
-            steps += chunk
-            res = sim.error_norms(ue, check=False)["residual"]
-        e64 = sim.error_norms(ue, check=False)["l2_rel"]
-        del sim
+        r1, r2 = 10.0 * n / 64, 28.0 * n / 64
+        tau = (r2 - r1) ** 2 / (np.pi ** 2 * w["nu"])
+        n32 = int(np.ceil(10 * tau / chunk)) * chunk
         s32 = build_sim(w, "f32", torch, stream)
         s32.init_equilibrium(None, ue)
-        s32.step(steps)
-        e32 = s32.error_norms(ue, check=False)["l2_rel"]
+        s32.step(n32 - chunk)
+        s32.error_norms(ue, check=False)
+        s32.step(chunk)
+        nrm = s32.error_norms(ue, check=False)
+        out["f32"][str(n)] = {"E_r": nrm["l2_rel"], "steps": n32, "residual": nrm["residual"]}
+        f = s32.get_populations()
         del s32
-        out["f64"][str(n)] = {"E_r": e64, "steps": steps, "residual": res}
-        out["f32"][str(n)] = {"E_r": e32, "steps": steps}
+        s64 = build_sim(w, "f64", torch, stream)
+        s64.set_populations(f)
+        s64.error_norms(ue, check=False)
+        steps, res = 0, 1.0
+        while res >= tol and steps < args.refine_max_steps:
+            s64.step(chunk)
+            steps += chunk
+            res = s64.error_norms(ue, check=False)["residual"]
+        e64 = s64.error_norms(ue, check=False)["l2_rel"]
+        del s64
+        out["f64"][str(n)] = {"E_r": e64, "steps_after_f32": steps, "residual": res,
+                              "converged": bool(res < tol)}
 
-    def order(prec):
-        e = [out[prec][str(n)]["E_r"] for n in sizes]
-        return float(-np.polyfit(np.log(sizes), np.log(e), 1)[0]) if len(sizes) > 1 else None
-    out["order_f64"] = order("f64")
-    out["order_f32"] = order("f32")
+    def order(prec, ns):
+        e = [out[prec][str(n)]["E_r"] for n in ns]
+        return float(-np.polyfit(np.log(ns), np.log(e), 1)[0]) if len(ns) > 1 else None
+    out["order_f64"] = order("f64", sizes)
+    out["order_f32"] = order("f32", sizes)
+    out["order_f64_to_512"] = order("f64", [n for n in sizes if n <= 512])
+    # the size from which FP32's error leaves FP64's by more than 10 %
+    out["f32_matched"] = {str(n): bool(abs(out["f32"][str(n)]["E_r"] - out["f64"][str(n)]["E_r"])
+                                       <= 0.1 * out["f64"][str(n)]["E_r"]) for n in sizes}
     out["seconds"] = round(time.perf_counter() - t_start, 1)
     if args.refine_mlups_n > 0:
         w = W.couette_config(args.refine_mlups_n)
@@ -485,11 +601,11 @@ def run_taylor_green(args, torch, stream):
     through lbm_set_wall_factor, l = gamma): E_r at T = 1/U0 for h = 1/40 .. 1/200 at
     s_nu = 1 and 1.99, FP64, and the least-squares order."""
     from paper_1712_08288_gb300 import workloads as W
-    sizes = [n for n in (40, 80, 120, 160, 200) if n <= args.tg_max]
+    sizes = [int(n) for n in args.tg_sizes.split(",") if n and int(n) <= args.tg_max]
     out = {"workload": "Taylor-Green vortex in the disc of Sec. 3.2, nu 0.002, U0 0.05, T = 1/U0",
            "inv_h": sizes}
     t_start = time.perf_counter()
-    for s_nu in (1.0, 1.99):
+    for s_nu in [float(v) for v in args.tg_snu.split(",") if v]:
         errs, steps = [], []
         for n in sizes:
             w = W.taylor_green_disc(n, s_nu)
@@ -513,10 +629,10 @@ def run_adjoint(args, torch, stream):
     (64.37, 63.71, 64.13), body force 1e-6 along x, s_nu = 1): loss = sum over the slab
     96 <= x < 104 of |u - u_target|^2 after K steps from rest, u_target from a run with
     every wall fraction raised by 0.05 (clamped to 1) and s_nu scaled by 1.02.
-    FP32 timing: lbm_adjoint (forward with checkpoints + recompute + adjoint sweep),
-    after one warm-up call that allocates its workspace, against lbm_step over the
-    same K steps.  FP64 check: dJ/ds_nu (sum over the
-    viscous rows) against central differences with h = 1e-4."""
+    Timing (after one warm-up call that allocates the workspace): the forward half
+    lbm_adjoint_forward against lbm_step over the same K steps, and the backward
+    half lbm_adjoint_backward against the forward half.  FP64 check: dJ/ds_nu (sum
+    over the viscous rows) against central differences with h = 1e-4."""
     from paper_1712_08288_gb300 import workloads as W
     n, K = args.adjoint_L, args.adjoint_steps
     c = (64.37 * n / 128, 63.71 * n / 128, 64.13 * n / 128)
@@ -545,18 +661,27 @@ def run_adjoint(args, torch, stream):
         t0 = time.perf_counter()
         sim.step(K)
         torch.cuda.synchronize()
-        t_fwd = time.perf_counter() - t0
+        t_step = time.perf_counter() - t0
         sim.init_equilibrium()
         sim.adjoint(K, mask, ut)                # warm-up: allocates the adjoint's workspace
         sim.init_equilibrium()
         torch.cuda.synchronize()
+        # the two halves the autograd Function calls: lbm_adjoint_forward (the
+        # checkpointed run and the loss) and lbm_adjoint_backward (recompute and
+        # adjoint sweep)
         t0 = time.perf_counter()
-        J, gs, gq, gp = sim.adjoint(K, mask, ut)
+        J = sim.adjoint_forward(K, mask, ut)
         torch.cuda.synchronize()
-        t_adj = time.perf_counter() - t0
+        t_fwd = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        gs, gq, gp = sim.adjoint_backward()
+        torch.cuda.synchronize()
+        t_bwd = time.perf_counter() - t0
         out[prec] = {"J": J, "dJ_ds_nu": float(gs[viscous].sum()),
-                     "forward_s": round(t_fwd, 4), "adjoint_total_s": round(t_adj, 4),
-                     "backward_over_forward": round((t_adj - t_fwd) / t_fwd, 2),
+                     "lbm_step_s": round(t_step, 4), "forward_s": round(t_fwd, 4),
+                     "backward_s": round(t_bwd, 4),
+                     "forward_over_lbm_step": round(t_fwd / t_step, 3),
+                     "backward_over_forward": round(t_bwd / t_fwd, 2),
                      "checkpoints": int(np.ceil(K / np.ceil(np.sqrt(K))))}
         if prec == "f64":
             h = 1e-4
@@ -580,9 +705,7 @@ def run_adjoint(args, torch, stream):
     return out
 
 
-def _oracle_rate(L, steps, warmup):
-    """Run the oracle in a fresh single-threaded process; returns (MLUPS, seconds)."""
-    code = r"""
+_ORACLE_RUN = r"""
 import os, sys, time, json
 sys.path.insert(0, %r)
 import numpy as np
@@ -593,22 +716,52 @@ sim = O.Simulation(OL.D3Q19, w['shape'], w['S'], 1.0, w['solid'], w['links'], sc
                    force=w['force'], skew=w['skew'])
 sim.init_equilibrium(None, np.nan_to_num(w['u_exact']))
 sim.step(%d)
-t = time.perf_counter(); sim.step(%d); dt = time.perf_counter() - t
+start_at = %r
+while start_at and time.time() < start_at:
+    time.sleep(0.01)
+t0 = time.time(); p0 = time.perf_counter(); sim.step(%d); dt = time.perf_counter() - p0
 nf = int((~w['solid']).sum())
-print(json.dumps({'mlups': nf * %d / dt / 1e6, 'seconds': dt, 'fluid': nf}))
-""" % (ROOT, L, SCHEME, warmup, steps, steps)
+print(json.dumps({'mlups': nf * %d / dt / 1e6, 'seconds': dt, 'fluid': nf, 't0': t0, 't1': t0 + dt}))
+"""
+
+
+def _oracle_procs(L, steps, warmup, nproc):
+    """Run the oracle in nproc fresh single-threaded processes started together
+    (each steps its own copy of the sample); returns their JSON records."""
+    start_at = time.time() + 20.0 if nproc > 1 else 0.0
+    code = _ORACLE_RUN % (ROOT, L, SCHEME, warmup, start_at, steps, steps)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
-    if r.returncode != 0:
-        raise RuntimeError(r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+    procs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True, env=env) for _ in range(nproc)]
+    out = []
+    for pr in procs:
+        so, se = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError(se[-2000:])
+        out.append(json.loads(so.strip().splitlines()[-1]))
+    return out
+
+
+def _oracle_rate(L, steps, warmup):
+    """Run the oracle in one fresh single-threaded process; returns its record."""
+    return _oracle_procs(L, steps, warmup, 1)[0]
 
 
 def cpu_baseline(L, steps):
-    res = _oracle_rate(L, steps, 1)
-    return {"value": round(res["mlups"], 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "FP64 numpy oracle, same pipe recipe at L=%d (%d fluid nodes), %d steps, "
-                      "%.1f s, single thread" % (L, res["fluid"], steps, res["seconds"])}
+    """The oracle as it stands on the host cores: one single-threaded process, and
+    one process per core (nproc) stepping its own copy of the same sample at the
+    same time (whole-host throughput)."""
+    one = _oracle_rate(L, steps, 1)
+    ncores = os.cpu_count() or 1
+    many = _oracle_procs(L, steps, 1, ncores)
+    wall = max(r["t1"] for r in many) - min(r["t0"] for r in many)
+    agg = sum(r["fluid"] * steps for r in many) / wall / 1e6
+    return {"value": round(agg, 4), "unit": "MLUPS", "cores": ncores, "kind": "oracle",
+            "sample": "FP64 numpy oracle, same pipe recipe at L=%d (%d fluid nodes), %d steps per "
+                      "process, %d single-threaded processes at once (nproc), %.1f s wall"
+                      % (L, one["fluid"], steps, ncores, wall),
+            "single_thread": {"value": round(one["mlups"], 4), "cores": 1,
+                              "seconds": round(one["seconds"], 2)}}
 
 
 def run_reference(args):
@@ -646,14 +799,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--L", type=int, default=256)
-    ap.add_argument("--accuracy-L", type=int, default=128)
+    ap.add_argument("--accuracy-sizes", default="64,128,256")
     ap.add_argument("--accuracy-steps", type=int, default=20000)
     ap.add_argument("--adjoint-L", type=int, default=128)
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--d3q15-steps", type=int, default=1000)
-    ap.add_argument("--refine-max", type=int, default=512)
+    ap.add_argument("--refine-max", type=int, default=1024)
     ap.add_argument("--tg-max", type=int, default=200)
-    ap.add_argument("--refine-max-steps", type=int, default=600000)
+    ap.add_argument("--tg-sizes", default="40,80,120,160,200")
+    ap.add_argument("--tg-snu", default="1,1.99")
+    ap.add_argument("--refine-max-steps", type=int, default=1500000)
     ap.add_argument("--refine-mlups-n", type=int, default=2048)
     ap.add_argument("--ensemble-count", type=int, default=96)
     ap.add_argument("--ensemble-steps", type=int, default=400)
