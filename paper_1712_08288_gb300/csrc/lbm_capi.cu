@@ -228,6 +228,7 @@ static void refresh_args(lbm_ctx *c) {
         a.koff_even[i] = L::opp(i) * S;
         a.koff_odd[i] = i * S + L::ex(i) + nxl * L::ey(i) + nxy * L::ez(i);
       }
+      a.kwrap = nxl * (1 + c->sy) + nxy * c->sz;
       return 0;
     });
   };

@@ -109,6 +109,10 @@ struct SweepArgs {
   // the node itself, odd step slot i of x + e_i (no wrap)
   long long koff_even[19];
   long long koff_odd[19];
+  // the odd-step store of node (0, y, z) across the x-wrap lands at koff_odd[i] +
+  // kwrap, that of node (nx-1, y, z) at koff_odd[i] - kwrap, when the skew-shifted
+  // rows stay inside the grid: kwrap = nx (1 + sy) + nx ny sz
+  long long kwrap;
   // when non-null, the sweep also writes every fluid node's pre-collision
   // deviations g_i(x, t) here, natural layout save[i*N + n] (adjoint recomputation)
   C *save = nullptr;

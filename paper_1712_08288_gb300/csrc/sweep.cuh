@@ -509,6 +509,25 @@ __device__ __forceinline__ void issue_tile(const SweepArgs<typename Storage<T>::
   if (src2) bulk_copy_g2s(dst2, src2, 16u, bar);
 }
 
+// A link's coefficients through the read-only (non-coherent) path.  They do not
+// change during a sweep, so the compiler may issue these loads ahead of the
+// boundary block's stores (which it could not do with plain loads, since a store
+// of the storage type may alias them); each load then costs one L2 round trip per
+// warp instead of one per cut direction in turn.
+template <class C>
+__device__ __forceinline__ LinkCoef<C> load_coef_nc(const LinkCoef<C> *p) {
+  LinkCoef<C> c;
+  if constexpr (sizeof(C) == 4) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    c.a = v.x; c.bb = v.y; c.c = v.z; c.w = v.w;
+  } else {
+    const double2 v0 = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 v1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    c.a = v0.x; c.bb = v0.y; c.c = v1.x; c.w = v1.y;
+  }
+  return c;
+}
+
 // resident blocks per SM the register budget is sized for
 #ifndef LBM_MINBLOCKS_F32
 #define LBM_MINBLOCKS_F32 5
@@ -687,17 +706,34 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
           if ((ex > 0 && xhi) || (ex < 0 && xlo)) continue;   // crosses the x-wrap
           Storage<T>::store(pn + (I)A.koff_odd[i], gp[i]);     // slot i of x + e_i
         }
+        // stores across the periodic x-wrap: when the skew-shifted rows (y +- sy +
+        // e_y, z +- sz + e_z) stay inside the grid, the target is the regular odd-step
+        // offset moved by +-kwrap; otherwise every row index is wrapped
         if (xlo) {
+          const int ys = y + sy, zs = z + sz;
+          if (ys >= 1 && ys <= A.ny - 2 && (L::D == 2 || (zs >= 1 && zs <= A.nz - 2))) {
 #pragma unroll
-          for (int i = 0; i < Q; ++i)
-            if (L::ex(i) < 0)
-              Storage<T>::store(pop + (I)i * S + across(nxm1, sy + L::ey(i), sz + L::ez(i)), gp[i]);
+            for (int i = 0; i < Q; ++i)
+              if (L::ex(i) < 0) Storage<T>::store(pn + (I)(A.koff_odd[i] + A.kwrap), gp[i]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+              if (L::ex(i) < 0)
+                Storage<T>::store(pop + (I)i * S + across(nxm1, sy + L::ey(i), sz + L::ez(i)), gp[i]);
+          }
         }
         if (xhi) {
+          const int ys = y - sy, zs = z - sz;
+          if (ys >= 1 && ys <= A.ny - 2 && (L::D == 2 || (zs >= 1 && zs <= A.nz - 2))) {
 #pragma unroll
-          for (int i = 0; i < Q; ++i)
-            if (L::ex(i) > 0)
-              Storage<T>::store(pop + (I)i * S + across(0, -sy + L::ey(i), -sz + L::ez(i)), gp[i]);
+            for (int i = 0; i < Q; ++i)
+              if (L::ex(i) > 0) Storage<T>::store(pn + (I)(A.koff_odd[i] - A.kwrap), gp[i]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+              if (L::ex(i) > 0)
+                Storage<T>::store(pop + (I)i * S + across(0, -sy + L::ey(i), -sz + L::ez(i)), gp[i]);
+          }
         }
       } else {
         // rows of the tile touch a periodic edge in y or z: wrap every neighbour
@@ -716,7 +752,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
       for (int dd = 1; dd < Q; ++dd) {
         if (bmask & (1u << dd)) {
           const int kk = boff + __popc(bmask & ((1u << dd) - 1u));
-          const LinkCoef<C> c = coef[kk];
+          const LinkCoef<C> c = load_coef_nc(coef + kk);
           const int i = L::opp(dd);
           const C v = A.one_minus_b * g[i] + c.a * g[dd] + c.bb * gp[i] + c.c * gp[dd] + c.w * A.wfac;
           if (!ODD) Storage<T>::store(lnk + kk, v);          // read by the next odd step
