@@ -201,14 +201,18 @@ __device__ __forceinline__ void collide_d3q19(const C (&g)[19], C (&gp)[19], con
   }
 }
 
-// MRT collision with the body force, deviation variables, g -> gp.
-template <class L, class C>
+// MRT collision with the body force, deviation variables, g -> gp.  T is the
+// storage type (it selects the form of the D3Q19 collision).
+template <class L, class C, class T = C>
 __device__ __forceinline__ void collide(const C (&g)[L::Q], C (&gp)[L::Q], const SweepArgs<C> &a,
                                         C &drho_out) {
-  if constexpr (std::is_same_v<L, D3Q19> && sizeof(C) == 8) {
-    // FP64 is ALU-bound on this GPU: the factored form is 22 % faster there.  FP32 is
-    // bandwidth-bound and keeps the generic form, whose rounding tracks FP64 closer
-    // (E_r 0.2 % from FP64 after 20000 steps, against 2.3 % with the factored form).
+  if constexpr (std::is_same_v<L, D3Q19> && (sizeof(C) == 8 || sizeof(T) == 2)) {
+    // The factored form where the sweep is bound by instruction issue: FP64 (the FP64
+    // pipe; 22 % faster) and 16-bit storage (half the bytes of FP32, the same
+    // instructions; 8 % faster).  FP32 storage is bound by memory traffic, runs at
+    // the same speed with either form, and keeps the generic form, whose rounding
+    // tracks FP64 closer (E_r 0.2 % from FP64 after 20000 steps, against 2.3 % with
+    // the factored form).
     collide_d3q19<C>(g, gp, a, drho_out);
     return;
   }
@@ -688,7 +692,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
 
     C gp[Q];
     C drho;
-    collide<L, C>(g, gp, A, drho);
+    collide<L, C, T>(g, gp, A, drho);
     if (!(fabs(drho) < C(1e6))) atomicOr(A.status, 1);
 
     T *const pn = pop + n;

@@ -211,7 +211,7 @@ def couette_config(n):
     return w
 
 
-def taylor_green_disc(inv_h, s_nu, nu=0.002, U0=0.05, rho0=1.0, lattice="D2Q9"):
+def taylor_green_disc(inv_h, s_nu, nu=0.002, U0=0.05, rho0=1.0, lattice="D2Q9", shift=(0.0, 0.0)):
     """The paper's Taylor-Green vortex in the disc (x - 1/2)^2 + (y - 1/2)^2 <= 1/16
     (Sec. 3.2): nu = 0.002, U0 = 0.05, p0 = rho0 c_s^2, h = 1/inv_h, delta_t = eta h^2
     with eta = (1/s_nu - 1/2)/(3 nu), no force.
@@ -222,6 +222,11 @@ def taylor_green_disc(inv_h, s_nu, nu=0.002, U0=0.05, rho0=1.0, lattice="D2Q9"):
     link is the analytic velocity at its wall point x_b = x_f + q e_d at t = 0; the
     whole field decays as exp(-8 pi^2 nu t), so at step n it is the t = 0 value times
     decay**n (decay = exp(-8 pi^2 nu eta h^2)).  T = 1/U0 is `steps` steps (rounded).
+
+    shift moves the disc by (sx, sy) physical units against the lattice (the velocity
+    field is 1-periodic, so the shifted problem has the same analytic solution); with
+    a nonzero shift the rim test is the plain distance test (exact ties have measure
+    zero), and the disc must stay inside the unit square.
     """
     n = int(inv_h) + 1
     h = 1.0 / inv_h
@@ -233,12 +238,17 @@ def taylor_green_disc(inv_h, s_nu, nu=0.002, U0=0.05, rho0=1.0, lattice="D2Q9"):
     # in units of h the disc is 4((2i - m)^2 + (2j - m)^2) < m^2 with m = inv_h: an
     # exact integer test, so nodes on the rim are solid
     m = int(inv_h)
-    solid = ~(4 * ((2 * x - m) ** 2 + (2 * y - m) ** 2) < m * m)
+    cx, cy = 0.5 + float(shift[0]), 0.5 + float(shift[1])
+    if shift[0] == 0 and shift[1] == 0:
+        solid = ~(4 * ((2 * x - m) ** 2 + (2 * y - m) ** 2) < m * m)
+    else:
+        assert R + max(abs(shift[0]), abs(shift[1])) < 0.5 - 2 * h
+        solid = ~((X - cx) ** 2 + (Y - cy) ** 2 < R * R)
     node, d = cut_links(lattice, shape, (0, 0), solid)
     px, py = X[node], Y[node]
     dx = E[d, 0].astype(np.float64) * h
     dy = E[d, 1].astype(np.float64) * h
-    wx, wy = px - 0.5, py - 0.5
+    wx, wy = px - cx, py - cy
     q = _first_root(dx * dx + dy * dy, 2 * (dx * wx + dy * wy), wx * wx + wy * wy - R * R)
     xb, yb = px + q * dx, py + q * dy
     eta = (1.0 / s_nu - 0.5) / (3.0 * nu)
