@@ -19,6 +19,7 @@ import pytest
 
 from oracle import lattices as OL
 from oracle import lbm as O
+from paper_1712_08288_gb300 import binding as B
 from paper_1712_08288_gb300 import workloads as W
 
 from gpu_common import check_close, deviation, gpu_sim, oracle_sim, patch_reference, require_gpu
@@ -358,3 +359,41 @@ def test_full_size_d3q15_pipe_sampled_nodes():
     g.step(2)
     check_close(deviation(g.get_populations()[:, centres], lat), deviation(want, lat), TOL32_STEPS,
                 None, "D3Q15 f32 L=256 samples")
+
+
+def test_64bit_slot_indices_periodic_box():
+    """A grid whose population slots need 64-bit element indices (Q * S >= 2^31: a
+    484^3 D3Q19 periodic box, 113M nodes, FP32): the sweep's long-index
+    instantiations (even and odd steps) against the oracle on sampled nodes.  A
+    density perturbation makes the field non-uniform; after 2 steps rho and u of 24
+    sampled nodes are compared with the oracle's patch evaluation."""
+    torch = require_gpu()
+    n = 484
+    N = n ** 3
+    assert 19 * N >= 2 ** 31
+    lat = OL.D3Q19
+    x = np.arange(N) % n
+    y = (np.arange(N) // n) % n
+    z = np.arange(N) // (n * n)
+    rho = 1.0 + 1e-3 * (np.sin(2 * np.pi * x / 37.0) + np.cos(2 * np.pi * y / 53.0) * np.sin(2 * np.pi * z / 29.0))
+    del x, y, z
+    S = W.relaxation_rates("D3Q19", 1.3)
+    g = B.Lbm("D3Q19", (n, n, n), S, "f32")
+    g.set_force((1e-5, -2e-6, 3e-6))
+    g.init_equilibrium(rho, None)
+    g.step(2)
+    rho_g, u_g = g.moments()
+    g.close()
+    w = dict(lattice="D3Q19", shape=(n, n, n), skew=(0, 0), solid=np.zeros(N, bool),
+             links=dict(node=np.zeros(0, np.int64), d=np.zeros(0, np.int64), q=np.zeros(0),
+                        uw=np.zeros((0, 3))),
+             S=S, rho0=1.0, force=(1e-5, -2e-6, 3e-6))
+    rng = np.random.default_rng(24)
+    centres = rng.choice(N, 24, replace=False)
+    f0_fn = lambda idx: O.equilibrium(lat, rho[idx], np.zeros((3, len(idx))), 1.0)
+    want = patch_reference(w, f0_fn, centres, 2, (0, 1, 0, 1.0))
+    e = lat.e.T.astype(float)
+    rho_w = want.sum(axis=0)
+    u_w = (e @ want).T / 1.0 + 0.5 * np.array([1e-5, -2e-6, 3e-6])
+    check_close(rho_g[centres] - 1.0, rho_w - 1.0, TOL32_STEPS, None, "64-bit index rho - 1")
+    check_close(u_g[centres], u_w, 1e-5, None, "64-bit index u")
