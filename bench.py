@@ -503,7 +503,7 @@ def run_ensemble(args, torch, stream):
     sims = fresh()
     batch = B.Batch(sims)
     batch.set_stream(stream.cuda_stream)
-    order, blocks, split = batch.tune(20)
+    order, blocks, split, tile_w = batch.tune(20)
     batch.step(4)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -521,6 +521,7 @@ def run_ensemble(args, torch, stream):
             "alg_GBs": round(2 * 9 * 4 * nf * K / (ms_batch * 1e-3) / 1e9, 1),
             "frac_of_hbm": round(2 * 9 * 4 * nf * K / (ms_batch * 1e-3) / 1e9 / peaks()[0], 4),
             "tuned": {"order": B.Batch.ORDERS[order], "blocks_per_sm": blocks, "split_by_class": bool(split),
+                      "tile_w": tile_w,
                       "launches_per_step": q["launches_per_step"], "tiles": q["tiles"]},
             "workload": "D2Q9 circular Couette ensemble, seed 0, n ~ U{48..768}, FP32 deviations"}
 

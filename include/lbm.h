@@ -291,20 +291,27 @@ int lbm_adjoint_backward(lbm_ctx *ctx, double *grad_s, double *grad_q, double *g
  * members -- rows starting on 16-byte boundaries or not, skewed x-wrap or not --
  * its own launch of the sweep specialised for it (aligned windows, no skew
  * handling), all inside the same graph; 0 runs every member through the general
- * sweep (unaligned windows, skew), one launch per step.  Grids whose slots need
- * 64-bit indices always take the general sweep.  lbm_batch_tune times every
- * (split, order, blocks) combination over trial_steps steps, keeps the fastest
- * and restores the contexts' state, so tuning does not advance the simulations.
- * lbm_batch_query also reports the kernel launches one step takes. */
+ * sweep (unaligned windows, skew), one launch per step.  tile_w: nodes per warp
+ * tile, 64 (the default, as for a single context) or 32 (every 64-node tile cut
+ * in halves, halves without fluid dropped: fewer idle lanes on small or thin
+ * members, more pipeline work per node).  The results do not depend on order,
+ * blocks, split or tile_w, bit for bit.  Grids whose slots need 64-bit indices
+ * always take the general sweep in 64-node tiles.  lbm_batch_tune times every
+ * (tile_w, split, order, blocks) combination over trial_steps steps, keeps the
+ * fastest and restores the contexts' state, so tuning does not advance the
+ * simulations; any output pointer may be NULL.  lbm_batch_query also reports the
+ * kernel launches one step takes and the tile width in use.  LBM_EINVAL for a
+ * value out of range. */
 typedef struct lbm_batch lbm_batch;
 int lbm_batch_create(lbm_batch **out, int n, lbm_ctx *const *ctxs);
 int lbm_batch_destroy(lbm_batch *batch);
 int lbm_batch_set_stream(lbm_batch *batch, void *cuda_stream);
-int lbm_batch_set_config(lbm_batch *batch, int order, int blocks_per_sm, int split);
-int lbm_batch_tune(lbm_batch *batch, int trial_steps, int *order, int *blocks_per_sm, int *split);
+int lbm_batch_set_config(lbm_batch *batch, int order, int blocks_per_sm, int split, int tile_w);
+int lbm_batch_tune(lbm_batch *batch, int trial_steps, int *order, int *blocks_per_sm, int *split,
+                   int *tile_w);
 int lbm_batch_step(lbm_batch *batch, int n);
 int lbm_batch_query(const lbm_batch *batch, int *n_contexts, int64_t *tiles, int *order,
-                    int *blocks_per_sm, int *launches_per_step);
+                    int *blocks_per_sm, int *launches_per_step, int *tile_w);
 const char *lbm_batch_last_error(const lbm_batch *batch);
 
 /* The current device's FP64 fused multiply-add rate in GFLOP/s (an FMA counted as

@@ -73,10 +73,10 @@ def load_library(path=LIB_PATH):
         "lbm_batch_create": (I, [ct.POINTER(P), I, P]),
         "lbm_batch_destroy": (I, [P]),
         "lbm_batch_set_stream": (I, [P, P]),
-        "lbm_batch_set_config": (I, [P, I, I, I]),
-        "lbm_batch_tune": (I, [P, I, P, P, P]),
+        "lbm_batch_set_config": (I, [P, I, I, I, I]),
+        "lbm_batch_tune": (I, [P, I, P, P, P, P]),
         "lbm_batch_step": (I, [P, I]),
-        "lbm_batch_query": (I, [P, P, P, P, P, P]),
+        "lbm_batch_query": (I, [P, P, P, P, P, P, P]),
         "lbm_batch_last_error": (ct.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -349,24 +349,26 @@ class Batch:
     def set_stream(self, stream_handle):
         self._check(self._lib.lbm_batch_set_stream(self.h, ct.c_void_p(stream_handle)))
 
-    def set_config(self, order, blocks_per_sm=0, split=1):
-        self._check(self._lib.lbm_batch_set_config(self.h, int(order), int(blocks_per_sm), int(split)))
+    def set_config(self, order, blocks_per_sm=0, split=1, tile_w=64):
+        self._check(self._lib.lbm_batch_set_config(self.h, int(order), int(blocks_per_sm), int(split),
+                                                   int(tile_w)))
 
     def tune(self, trial_steps=20):
-        """lbm_batch_tune: (order, blocks_per_sm, split) of the fastest configuration."""
-        o, b, sp = ct.c_int(), ct.c_int(), ct.c_int()
-        self._check(self._lib.lbm_batch_tune(self.h, int(trial_steps), ct.byref(o), ct.byref(b), ct.byref(sp)))
-        return o.value, b.value, sp.value
+        """lbm_batch_tune: (order, blocks_per_sm, split, tile_w) of the fastest configuration."""
+        o, b, sp, w = ct.c_int(), ct.c_int(), ct.c_int(), ct.c_int()
+        self._check(self._lib.lbm_batch_tune(self.h, int(trial_steps), ct.byref(o), ct.byref(b), ct.byref(sp),
+                                             ct.byref(w)))
+        return o.value, b.value, sp.value, w.value
 
     def step(self, n=1):
         self._check(self._lib.lbm_batch_step(self.h, int(n)))
 
     def query(self):
-        n, t, o, b, k = ct.c_int(), ct.c_int64(), ct.c_int(), ct.c_int(), ct.c_int()
+        n, t, o, b, k, w = ct.c_int(), ct.c_int64(), ct.c_int(), ct.c_int(), ct.c_int(), ct.c_int()
         self._check(self._lib.lbm_batch_query(self.h, ct.byref(n), ct.byref(t), ct.byref(o), ct.byref(b),
-                                              ct.byref(k)))
+                                              ct.byref(k), ct.byref(w)))
         return dict(contexts=n.value, tiles=t.value, order=o.value, blocks_per_sm=b.value,
-                    launches_per_step=k.value)
+                    launches_per_step=k.value, tile_w=w.value)
 
     def close(self):
         if getattr(self, "h", None):

@@ -26,12 +26,12 @@ cudaError_t launch_sweep_d3q15(int, bool, const SweepArgs<double> &, const Sweep
                                const TileDesc *, int, int, cudaStream_t);
 int error_norms_noalloc(int device, int lattice, int precision, const AuxArgs &a, bool odd,
                         const double *u_ref, double *out, cudaStream_t st, const char **why);
-cudaError_t launch_sweep_batch_d2q9(int, bool, const void *, const TileDesc *, const int *, int,
-                                   bool, bool, bool, int, cudaStream_t, bool);
-cudaError_t launch_sweep_batch_d3q19(int, bool, const void *, const TileDesc *, const int *, int,
-                                    bool, bool, bool, int, cudaStream_t, bool);
-cudaError_t launch_sweep_batch_d3q15(int, bool, const void *, const TileDesc *, const int *, int,
-                                    bool, bool, bool, int, cudaStream_t, bool);
+cudaError_t launch_sweep_batch_d2q9(int, int, bool, const void *, const TileDesc *, const int *,
+                                   int, bool, bool, bool, int, cudaStream_t, bool);
+cudaError_t launch_sweep_batch_d3q19(int, int, bool, const void *, const TileDesc *, const int *,
+                                   int, bool, bool, bool, int, cudaStream_t, bool);
+cudaError_t launch_sweep_batch_d3q15(int, int, bool, const void *, const TileDesc *, const int *,
+                                   int, bool, bool, bool, int, cudaStream_t, bool);
 cudaError_t launch_sweep(int lattice, int precision, bool odd, const SweepArgs<double> &a64,
                          const SweepArgs<float> &a32, const TileDesc *tiles, int n_tiles, int bx,
                          cudaStream_t st) {
@@ -1250,6 +1250,7 @@ struct lbm_batch {
   BatchList lists[kBatchClasses];  // tile lists per kernel class (batch_upload)
   int n_tiles = 0;
   bool split = true;             // one launch per kernel class (lbm_batch_set_config)
+  int tile_w = kTileW;           // nodes per tile in the lists: kTileW, or 32 (half tiles)
   bool big = false;
   int order = 1;                 // 0 context-major, 1 round-robin, 2 largest context first
   int blocks_per_sm = 0;         // 0: as many as fit
@@ -1292,6 +1293,27 @@ static void batch_drop_graph(lbm_batch *b) {
 static bool member_aligned(const lbm_ctx *c) {
   return ((long long)c->nx * store_bytes(c->precision)) % 16 == 0;
 }
+
+// A member's tiles cut into 32-node halves; halves without a fluid node are dropped.
+// A half keeps the tile's link-buffer base (its records' offsets are relative to it);
+// the second half's records start after the first half's.  Lanes past a half are
+// marked solid.
+static void half_tiles(const std::vector<TileDesc> &in, std::vector<TileDesc> &out) {
+  constexpr uint64_t kLo = 0xffffffffull;
+  out.clear();
+  out.reserve(2 * in.size());
+  for (const TileDesc &d : in) {
+    TileDesc a = d, h = d;
+    a.solid = d.solid | ~kLo;
+    a.bnd = d.bnd & kLo;
+    h.x0 = d.x0 + 32;
+    h.rb = d.rb + __builtin_popcountll(d.bnd & kLo);
+    h.solid = (d.solid >> 32) | ~kLo;
+    h.bnd = d.bnd >> 32;
+    if ((a.solid & kLo) != kLo) out.push_back(a);
+    if ((h.solid & kLo) != kLo) out.push_back(h);
+  }
+}
 static int batch_upload(lbm_batch *b) {
   const int n = (int)b->ctx.size();
   b->big = false;
@@ -1303,11 +1325,16 @@ static int batch_upload(lbm_batch *b) {
       const lbm_ctx *c = b->ctx[k];
       cls_of[k] = (member_aligned(c) ? 2 : 0) + ((c->sy != 0 || c->sz != 0) ? 1 : 0);
     }
+  // the members' tiles in the batch's tile width (64-bit slot indices: 64 only)
+  const bool halves = b->tile_w == 32 && !b->big;
+  std::vector<std::vector<TileDesc>> halved(halves ? n : 0);
+  for (int k = 0; k < (halves ? n : 0); ++k) half_tiles(b->host_tiles[k], halved[k]);
+  const std::vector<std::vector<TileDesc>> &mt = halves ? halved : b->host_tiles;
   std::vector<int> ctx_order(n);
   for (int k = 0; k < n; ++k) ctx_order[k] = k;
   if (b->order == 2)
     std::stable_sort(ctx_order.begin(), ctx_order.end(), [&](int p, int q) {
-      return b->host_tiles[p].size() > b->host_tiles[q].size();
+      return mt[p].size() > mt[q].size();
     });
   b->n_tiles = 0;
   for (int cl = 0; cl < kBatchClasses; ++cl) {
@@ -1321,8 +1348,8 @@ static int batch_upload(lbm_batch *b) {
       while (more) {
         more = false;
         for (int k : ctx_order)
-          if (cls_of[k] == cl && pos[k] < b->host_tiles[k].size()) {
-            t.push_back(b->host_tiles[k][pos[k]++]);
+          if (cls_of[k] == cl && pos[k] < mt[k].size()) {
+            t.push_back(mt[k][pos[k]++]);
             ti.push_back(k);
             more = true;
           }
@@ -1330,7 +1357,7 @@ static int batch_upload(lbm_batch *b) {
     } else {
       for (int k : ctx_order)
         if (cls_of[k] == cl)
-          for (const TileDesc &d : b->host_tiles[k]) {
+          for (const TileDesc &d : mt[k]) {
             t.push_back(d);
             ti.push_back(k);
           }
@@ -1391,15 +1418,15 @@ static cudaError_t batch_launch(lbm_batch *b, bool odd, bool prepare_only) {
     cudaError_t e;
     switch (b->lattice) {
       case LBM_D2Q9:
-        e = launch_sweep_batch_d2q9(b->precision, odd, b->inst, bl.tiles, bl.tile_inst, bl.n, b->big,
+        e = launch_sweep_batch_d2q9(b->precision, b->big ? kTileW : b->tile_w, odd, b->inst, bl.tiles, bl.tile_inst, bl.n, b->big,
                                     aligned, skew, b->blocks_per_sm, b->stream, prepare_only);
         break;
       case LBM_D3Q15:
-        e = launch_sweep_batch_d3q15(b->precision, odd, b->inst, bl.tiles, bl.tile_inst, bl.n, b->big,
+        e = launch_sweep_batch_d3q15(b->precision, b->big ? kTileW : b->tile_w, odd, b->inst, bl.tiles, bl.tile_inst, bl.n, b->big,
                                      aligned, skew, b->blocks_per_sm, b->stream, prepare_only);
         break;
       default:
-        e = launch_sweep_batch_d3q19(b->precision, odd, b->inst, bl.tiles, bl.tile_inst, bl.n, b->big,
+        e = launch_sweep_batch_d3q19(b->precision, b->big ? kTileW : b->tile_w, odd, b->inst, bl.tiles, bl.tile_inst, bl.n, b->big,
                                      aligned, skew, b->blocks_per_sm, b->stream, prepare_only);
     }
     if (e != cudaSuccess) return e;
@@ -1489,15 +1516,18 @@ int lbm_batch_set_stream(lbm_batch *b, void *stream) {
   return LBM_OK;
 }
 
-int lbm_batch_set_config(lbm_batch *b, int order, int blocks_per_sm, int split) {
+int lbm_batch_set_config(lbm_batch *b, int order, int blocks_per_sm, int split, int tile_w) {
   if (!b) return LBM_EINVAL;
-  if (order < 0 || order > 2 || blocks_per_sm < 0 || blocks_per_sm > 32 || split < 0 || split > 1)
+  if (order < 0 || order > 2 || blocks_per_sm < 0 || blocks_per_sm > 32 || split < 0 || split > 1 ||
+      (tile_w != 32 && tile_w != 64))
     return bfail(b, LBM_EINVAL,
-                 "lbm_batch_set_config: order in 0..2, blocks_per_sm in 0..32, split 0 or 1");
+                 "lbm_batch_set_config: order in 0..2, blocks_per_sm in 0..32, split 0 or 1, "
+                 "tile_w 32 or 64");
   DeviceGuard dg(b->device);
   b->order = order;
   b->blocks_per_sm = blocks_per_sm;
   b->split = split != 0;
+  b->tile_w = tile_w;
   batch_drop_graph(b);
   return batch_upload(b);
 }
@@ -1554,7 +1584,8 @@ int lbm_batch_step(lbm_batch *b, int n) {
   return LBM_OK;
 }
 
-int lbm_batch_tune(lbm_batch *b, int trial_steps, int *order_out, int *blocks_out, int *split_out) {
+int lbm_batch_tune(lbm_batch *b, int trial_steps, int *order_out, int *blocks_out, int *split_out,
+                   int *tile_w_out) {
   if (!b) return LBM_EINVAL;
   if (trial_steps < 2) return bfail(b, LBM_EINVAL, "lbm_batch_tune: trial_steps >= 2");
   trial_steps &= ~1;
@@ -1593,12 +1624,15 @@ int lbm_batch_tune(lbm_batch *b, int trial_steps, int *order_out, int *blocks_ou
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   const int orders[3] = {0, 1, 2};
   const int blocks[3] = {0, 4, 3};
+  const int widths[2] = {kTileW, 32};
   float best = 1e30f;
-  int best_o = b->order, best_b = b->blocks_per_sm;
+  int best_o = b->order, best_b = b->blocks_per_sm, best_w = b->tile_w;
   bool best_s = b->split;
+  for (int wi = 0; wi < (b->big ? 1 : 2) && e == cudaSuccess && rc == LBM_OK; ++wi)
   for (int si = 0; si < 2 && e == cudaSuccess && rc == LBM_OK; ++si)
-  for (int oi = 0; oi < 3 && e == cudaSuccess; ++oi)
+  for (int oi = 0; oi < 3 && e == cudaSuccess && rc == LBM_OK; ++oi)
     for (int bi = 0; bi < 3 && e == cudaSuccess; ++bi) {
+      b->tile_w = widths[wi];
       b->split = si == 0;
       b->order = orders[oi];
       b->blocks_per_sm = blocks[bi];
@@ -1615,6 +1649,7 @@ int lbm_batch_tune(lbm_batch *b, int trial_steps, int *order_out, int *blocks_ou
         best_o = orders[oi];
         best_b = blocks[bi];
         best_s = b->split;
+        best_w = b->tile_w;
       }
       if (e == cudaSuccess) e = copy_state(false);
     }
@@ -1627,16 +1662,18 @@ int lbm_batch_tune(lbm_batch *b, int trial_steps, int *order_out, int *blocks_ou
   b->order = best_o;
   b->blocks_per_sm = best_b;
   b->split = best_s;
+  b->tile_w = best_w;
   batch_drop_graph(b);
   if ((rc = batch_upload(b)) != LBM_OK) return rc;
   if (order_out) *order_out = best_o;
   if (blocks_out) *blocks_out = best_b;
   if (split_out) *split_out = best_s ? 1 : 0;
+  if (tile_w_out) *tile_w_out = best_w;
   return LBM_OK;
 }
 
 int lbm_batch_query(const lbm_batch *b, int *n_contexts, int64_t *tiles, int *order,
-                    int *blocks_per_sm, int *launches_per_step) {
+                    int *blocks_per_sm, int *launches_per_step, int *tile_w) {
   if (!b) return LBM_EINVAL;
   if (n_contexts) *n_contexts = (int)b->ctx.size();
   if (tiles) *tiles = b->n_tiles;
@@ -1647,6 +1684,7 @@ int lbm_batch_query(const lbm_batch *b, int *n_contexts, int64_t *tiles, int *or
     for (const BatchList &bl : b->lists) k += bl.n > 0 ? 1 : 0;
     *launches_per_step = k;
   }
+  if (tile_w) *tile_w = b->big ? kTileW : b->tile_w;
   return LBM_OK;
 }
 

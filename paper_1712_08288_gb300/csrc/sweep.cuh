@@ -376,30 +376,35 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
       : "memory");
 }
 
-// Work decomposition.  A tile is a run of kTileW nodes along x that holds at
-// least one fluid node; tiles are listed once per geometry.  A warp processes a
-// tile kNodesPerLane nodes per lane, one node after the other.  Every warp owns a
-// private pipeline of kStages shared-memory stages: stage s holds the Q population
-// row windows of one tile (each window up to kTileW + 16/sizeof(T) elements, start
-// aligned down to 16 bytes), filled by bulk copies that complete on the warp's own
-// mbarrier.  Warps never wait for each other.
+// Work decomposition.  A tile is a run of TW nodes along x (TW = kTileW = 64 for a
+// single context; batches may take 32) that holds at least one fluid node; tiles
+// are listed once per geometry.  A warp processes a tile TW/32 nodes per lane, one
+// node after the other.  Every warp owns a private pipeline of kStages shared-memory
+// stages: stage s holds the Q population row windows of one tile (each window up to
+// TW + 16/sizeof(T) elements, start aligned down to 16 bytes), filled by bulk copies
+// that complete on the warp's own mbarrier.  32-node tiles take more stages (3 for
+// 8- and 4-byte storage, 5 for 2-byte storage): a warp keeps most of its bytes in
+// flight while a block still fits the shared memory of the 64-node layout.  Warps
+// never wait for each other.
 constexpr int kWarpsPerBlock = 4;
 
 #ifndef LBM_STAGES_4B
 #define LBM_STAGES_4B 2
 #endif
-template <class T>
+template <class T, int TW = kTileW>
 struct StageShape {
-  static constexpr int kStages = sizeof(T) == 8 ? 2 : (sizeof(T) == 4 ? LBM_STAGES_4B : 3);
-  static constexpr int kWidth = kTileW + 16 / (int)sizeof(T);   // elements per window
-  static constexpr int kRecs = kTileW + 4;                       // record window (uint32)
+  static_assert(TW == 32 || TW == 64, "tiles are one or two nodes per lane wide");
+  static constexpr int kStages = TW == 64 ? (sizeof(T) == 8 ? 2 : (sizeof(T) == 4 ? LBM_STAGES_4B : 3))
+                                          : (sizeof(T) == 2 ? 5 : 3);
+  static constexpr int kWidth = TW + 16 / (int)sizeof(T);   // elements per window
+  static constexpr int kRecs = TW + 4;                       // record window (uint32)
 };
 
 // Byte layout of one stage: Q population windows, then the record window; after
 // all stages, the barriers and the offsets (Q + 1 per stage).
-template <class L, class T>
+template <class L, class T, int TW = kTileW>
 struct StageLayout {
-  using SS = StageShape<T>;
+  using SS = StageShape<T, TW>;
   static constexpr size_t kPop = (size_t)L::Q * SS::kWidth * sizeof(T);
   static constexpr size_t kRec = kPop;
   static constexpr size_t kStage = (kRec + SS::kRecs * sizeof(uint32_t) + 15) / 16 * 16;
@@ -410,12 +415,17 @@ struct StageLayout {
 
 // bytes of one warp's pipeline, a multiple of 128 so that every warp's stages
 // start 128-byte aligned
-template <class L, class T>
+template <class L, class T, int TW = kTileW>
 __host__ __device__ constexpr size_t warp_smem_bytes() {
-  using SL = StageLayout<L, T>;
-  return (SL::kOffs + StageShape<T>::kStages * SL::kNOff * sizeof(int) + 127) / 128 * 128;
+  using SL = StageLayout<L, T, TW>;
+  return (SL::kOffs + StageShape<T, TW>::kStages * SL::kNOff * sizeof(int) + 127) / 128 * 128;
 }
 static_assert(warp_smem_bytes<D3Q19, float>() % 128 == 0, "warp region alignment");
+static_assert(warp_smem_bytes<D3Q19, float, 32>() % 128 == 0, "warp region alignment");
+static_assert(StageLayout<D3Q19, float, 32>::kRec % 16 == 0 && StageLayout<D3Q19, double, 32>::kRec % 16 == 0 &&
+                  StageLayout<D3Q19, __half, 32>::kRec % 16 == 0 && StageLayout<D2Q9, __half, 32>::kRec % 16 == 0 &&
+                  StageLayout<D3Q15, __half, 32>::kRec % 16 == 0 && StageLayout<D3Q15, __half>::kRec % 16 == 0,
+              "record window alignment");
 static_assert(StageLayout<D3Q19, float>::kRec % 16 == 0 && StageLayout<D3Q19, double>::kRec % 16 == 0 &&
                   StageLayout<D3Q19, __half>::kRec % 16 == 0 && StageLayout<D2Q9, __half>::kRec % 16 == 0,
               "record window alignment");
@@ -433,19 +443,19 @@ __device__ __forceinline__ const char *align16(const E *p, int &off_elems) {
 }
 
 // One warp fills one stage with everything a tile needs, lane i issuing copy i:
-// lanes 0..Q-1 the population row windows (even step: window [x0, x0+kTileW) of slot
-// i in the tile's own row; odd step: [x0 - ex_i, x0 - ex_i + kTileW) of slot opp(i)
+// lanes 0..Q-1 the population row windows (even step: window [x0, x0+TW) of slot
+// i in the tile's own row; odd step: [x0 - ex_i, x0 - ex_i + TW) of slot opp(i)
 // in row (y - ey_i, z - ez_i)), lane Q the tile's packed boundary records.  Every
 // copy starts at the 16-byte boundary at or before its first element and covers its
 // window rounded up to 16 bytes; off[] records where each first element landed.
 // The offsets are stored before lane 0's arrive (release), so a lane that has
 // waited on the barrier sees them.  All lanes call.
-template <class L, class T, bool ODD, bool ALIGNED, class I>
+template <class L, class T, bool ODD, bool ALIGNED, class I, int TW>
 __device__ __forceinline__ void issue_tile(const SweepArgs<typename Storage<T>::C> &a,
                                            const TileDesc &td, unsigned char *stage, int *off,
                                            uint64_t *bar) {
-  using SL = StageLayout<L, T>;
-  constexpr int W = StageShape<T>::kWidth;
+  using SL = StageLayout<L, T, TW>;
+  constexpr int W = StageShape<T, TW>::kWidth;
   const int lane = threadIdx.x & 31;
   const int ty = td.yz & 0xffff, tz = td.yz >> 16;
   const char *src = nullptr, *src2 = nullptr;
@@ -465,7 +475,7 @@ __device__ __forceinline__ void issue_tile(const SweepArgs<typename Storage<T>::
     int o;
     src = align16(pop + elem, o);
     off[i] = o;
-    bytes = ((uint32_t)((o + kTileW) * (int)sizeof(T)) + 15u) & ~15u;
+    bytes = ((uint32_t)((o + TW) * (int)sizeof(T)) + 15u) & ~15u;
     dst = stage + (size_t)i * W * sizeof(T);
     if constexpr (ODD && ALIGNED) {
       // Windows that cross the periodic x-wrap (rows start on 16-byte boundaries):
@@ -476,17 +486,17 @@ __device__ __forceinline__ void issue_tile(const SweepArgs<typename Storage<T>::
       constexpr int E16 = 16 / (int)sizeof(T);
       const int ex = DirBits<L>::ex(i);
       const bool lo = ex > 0 && td.x0 == 0;
-      const bool hi = ex < 0 && td.x0 + kTileW > a.nx - 1;
+      const bool hi = ex < 0 && td.x0 + TW > a.nx - 1;
       if (lo || hi) {
         const int sy = lo ? a.sy : -a.sy, sz = lo ? a.sz : -a.sz;
         const int yw = wrap1(yy + sy, a.ny);
         const int zw = (L::D == 3) ? wrap1(zz + sz, a.nz) : 0;
         const I rw = (I)slot * (I)a.S + (I)a.nx * ((I)yw + (I)a.ny * zw);
         if (lo) {
-          // main copy: [0, kTileW) behind a 16-byte gap; chunk [nx-E16, nx) in the gap
+          // main copy: [0, TW) behind a 16-byte gap; chunk [nx-E16, nx) in the gap
           src = reinterpret_cast<const char *>(pop + elem + 1);
           dst = stage + ((size_t)i * W + E16) * sizeof(T);
-          bytes = kTileW * sizeof(T);
+          bytes = TW * sizeof(T);
           src2 = reinterpret_cast<const char *>(pop + rw + (a.nx - E16));
           dst2 = stage + (size_t)i * W * sizeof(T);
         } else {
@@ -536,12 +546,17 @@ __device__ __forceinline__ LinkCoef<C> load_coef_nc(const LinkCoef<C> *p) {
 #ifndef LBM_MINBLOCKS_F32
 #define LBM_MINBLOCKS_F32 5
 #endif
-template <class T>
+#ifndef LBM_MINBLOCKS_D2Q9
+#define LBM_MINBLOCKS_D2Q9 5
+#endif
+template <class L, class T>
 struct MinBlocks {
-  static constexpr int value = LBM_MINBLOCKS_F32;   // 5 x 128 threads: up to 96 registers
+  // 4- and 2-byte storage: 5 x 128 threads (up to 96 registers); D2Q9 has fewer
+  // populations per node to keep in registers
+  static constexpr int value = L::Q == 9 ? LBM_MINBLOCKS_D2Q9 : LBM_MINBLOCKS_F32;
 };
-template <>
-struct MinBlocks<double> {
+template <class L>
+struct MinBlocks<L, double> {
   static constexpr int value = 4;   // 4 x 128 threads: 128 registers (FP64 arithmetic)
 };
 
@@ -566,20 +581,22 @@ __device__ __forceinline__ const SweepArgs<C> &args_for(const SweepArgs<C> &a, c
   else return a;
 }
 
-template <class L, class T, bool ODD, bool SKEW, bool ALIGNED, class I, bool BATCH>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
+template <class L, class T, bool ODD, bool SKEW, bool ALIGNED, class I, bool BATCH, int TW = kTileW>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<L, T>::value)
     sweep_kernel(const SweepArgs<typename Storage<T>::C> a, const TileDesc *__restrict__ tiles,
                  int n_tiles, const SweepArgs<typename Storage<T>::C> *__restrict__ inst,
                  const int *__restrict__ tile_inst) {
   using C = typename Storage<T>::C;
-  using SL = StageLayout<L, T>;
+  using SL = StageLayout<L, T, TW>;
+  static_assert(SL::kRec % 16 == 0 && SL::kStage % 16 == 0, "bulk-copy destinations are 16-byte aligned");
+  static_assert((StageShape<T, TW>::kWidth * sizeof(T)) % 16 == 0, "window stride");
   constexpr int Q = L::Q;
-  constexpr int NS = StageShape<T>::kStages;
-  constexpr int W = StageShape<T>::kWidth;
+  constexpr int NS = StageShape<T, TW>::kStages;
+  constexpr int W = StageShape<T, TW>::kWidth;
   constexpr int NO = SL::kNOff;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned char *wsm = smem_raw + (size_t)warp * warp_smem_bytes<L, T>();
+  unsigned char *wsm = smem_raw + (size_t)warp * warp_smem_bytes<L, T, TW>();
   uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + SL::kBars);
   int *offs = reinterpret_cast<int *>(wsm + SL::kOffs);
 
@@ -593,7 +610,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
   for (int s = 0; s < NS; ++s) {
     const int tile = gw + s * nw;
     if (tile < n_tiles)
-      issue_tile<L, T, ODD, ALIGNED, I>(args_for<BATCH>(a, inst, tile_inst, tile), tiles[tile],
+      issue_tile<L, T, ODD, ALIGNED, I, TW>(args_for<BATCH>(a, inst, tile_inst, tile), tiles[tile],
                                wsm + s * SL::kStage, offs + s * NO, &bars[s]);
   }
 
@@ -624,7 +641,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
     const uint32_t *rec_s = reinterpret_cast<const uint32_t *>(stg + SL::kRec) + offs[s * NO + Q];
     const int row = A.nx * (y + A.ny * z);
 #pragma unroll 1
-    for (int j = 0; j < kNodesPerLane; ++j) {
+    for (int j = 0; j < TW / 32; ++j) {
     const int xl = j * 32 + lane;          // position inside the tile
     const int x = td.x0 + xl;
     const int n = row + x;
@@ -643,11 +660,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
       const int o = ALIGNED ? (ODD ? aligned_window_offset<T>(L::ex(i)) : 0) : offs[s * NO + i];
       g[i] = Storage<T>::load(st + i * W + o + xl);
     }
-    if (j == kNodesPerLane - 1) {
+    if (j == TW / 32 - 1) {
       __syncwarp();   // stage s consumed: refill it with the tile NS rounds ahead
       const int nt = tile + NS * nw;
       if (nt < n_tiles)
-        issue_tile<L, T, ODD, ALIGNED, I>(args_for<BATCH>(a, inst, tile_inst, nt), tiles[nt],
+        issue_tile<L, T, ODD, ALIGNED, I, TW>(args_for<BATCH>(a, inst, tile_inst, nt), tiles[nt],
                                  wsm + s * SL::kStage, offs + s * NO, &bars[s]);
     }
     if (solid) continue;
@@ -682,7 +699,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<T>::value)
 #pragma unroll
       for (int dd = 1; dd < Q; ++dd)
         if (bmask & (1u << dd))
-          g[L::opp(dd)] = Storage<T>::load(lnk + boff + __popc(bmask & ((1u << dd) - 1u)));
+            g[L::opp(dd)] = Storage<T>::load(lnk + boff + __popc(bmask & ((1u << dd) - 1u)));
     }
 
     if (A.save) {
@@ -837,25 +854,30 @@ cudaError_t launch_sweep_t(bool odd, const SweepArgs<typename Storage<T>::C> &a,
 // launch, each tile reading its member's arguments from the table.  aligned: every
 // member's rows start on 16-byte boundaries (aligned-window path); skew: some
 // member has a skewed x-wrap.  Batches whose slots need 64-bit indices (big) use
-// the general kernel (unaligned windows, skew) for every member.  prepare_only:
-// set up the kernel's launch attributes without launching (done once before a
-// stream capture).
-template <class L, class T>
+// the general kernel (unaligned windows, skew) for every member, in 64-node tiles.
+// TW: the width of the tiles in the list (64, or 32 for lists of half tiles).
+// prepare_only: set up the kernel's launch attributes without launching (done once
+// before a stream capture).
+template <class L, class T, int TW>
 cudaError_t launch_sweep_batch_t(bool odd, const SweepArgs<typename Storage<T>::C> *inst,
                                  const TileDesc *tiles, const int *tile_inst, int n_tiles,
                                  bool big, bool aligned, bool skew, int blocks_per_sm, cudaStream_t st,
                                  bool prepare_only) {
   if (n_tiles == 0) return cudaSuccess;
   using A = SweepArgs<typename Storage<T>::C>;
-  const size_t smem = kWarpsPerBlock * warp_smem_bytes<L, T>();
+  const size_t smem = kWarpsPerBlock * warp_smem_bytes<L, T, TW>();
   A dummy{};
   dummy.wait_polls = kWaitLimit;
-#define LBM_LAUNCH_B(O, S, AL, I)                                                                  \
-  launch_persistent<sweep_kernel<L, T, O, S, AL, I, true>>(dummy, tiles, n_tiles, smem, st, inst,  \
-                                                           tile_inst, blocks_per_sm, prepare_only)
+#define LBM_LAUNCH_B(O, S, AL, I)                                                                      \
+  launch_persistent<sweep_kernel<L, T, O, S, AL, I, true, TW>>(dummy, tiles, n_tiles, smem, st, inst,  \
+                                                               tile_inst, blocks_per_sm, prepare_only)
   if (big) {
-    if (odd) LBM_LAUNCH_B(true, true, false, long long);
-    else LBM_LAUNCH_B(false, false, false, long long);
+    if constexpr (TW != kTileW) {
+      return cudaErrorInvalidValue;   // 64-bit slot indices: 64-node tiles only
+    } else {
+      if (odd) LBM_LAUNCH_B(true, true, false, long long);
+      else LBM_LAUNCH_B(false, false, false, long long);
+    }
   } else if (!odd) {
     if (aligned) LBM_LAUNCH_B(false, false, true, int);
     else LBM_LAUNCH_B(false, false, false, int);

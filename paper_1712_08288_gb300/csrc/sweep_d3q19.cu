@@ -1,4 +1,5 @@
 // sweep_d3q19.cu -- D3Q19 instantiations of the fused collide / stream / boundary sweep
+// of a single context
 // (storage: FP64, FP32 deviations, BF16 deviations, FP16 deviations).
 #include "sweep.cuh"
 
@@ -12,18 +13,6 @@ cudaError_t launch_sweep_d3q19(int precision, bool odd, const SweepArgs<double> 
     case 1: return launch_sweep_t<D3Q19, float>(odd, a32, tiles, n_tiles, bx, st);
     case 2: return launch_sweep_t<D3Q19, __nv_bfloat16>(odd, a32, tiles, n_tiles, bx, st);
     case 3: return launch_sweep_t<D3Q19, __half>(odd, a32, tiles, n_tiles, bx, st);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-cudaError_t launch_sweep_batch_d3q19(int precision, bool odd, const void *inst, const TileDesc *tiles,
-                                 const int *tile_inst, int n_tiles, bool big, bool aligned, bool skew,
-                                 int blocks_per_sm, cudaStream_t st, bool prepare_only) {
-  switch (precision) {
-    case 0: return launch_sweep_batch_t<D3Q19, double>(odd, static_cast<const SweepArgs<double> *>(inst), tiles, tile_inst, n_tiles, big, aligned, skew, blocks_per_sm, st, prepare_only);
-    case 1: return launch_sweep_batch_t<D3Q19, float>(odd, static_cast<const SweepArgs<float> *>(inst), tiles, tile_inst, n_tiles, big, aligned, skew, blocks_per_sm, st, prepare_only);
-    case 2: return launch_sweep_batch_t<D3Q19, __nv_bfloat16>(odd, static_cast<const SweepArgs<float> *>(inst), tiles, tile_inst, n_tiles, big, aligned, skew, blocks_per_sm, st, prepare_only);
-    case 3: return launch_sweep_batch_t<D3Q19, __half>(odd, static_cast<const SweepArgs<float> *>(inst), tiles, tile_inst, n_tiles, big, aligned, skew, blocks_per_sm, st, prepare_only);
     default: return cudaErrorInvalidValue;
   }
 }

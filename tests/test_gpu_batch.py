@@ -1,6 +1,7 @@
 """Batched ensembles (lbm_batch_*): one persistent launch per step over the tiles of
 many contexts, replayed from a CUDA graph, must give exactly what stepping every
-context alone gives; tuning must leave the state untouched."""
+context alone gives, in 64-node tiles and in 32-node half tiles; tuning must leave
+the state untouched."""
 
 import numpy as np
 import pytest
@@ -37,9 +38,10 @@ def _make(ws, prec, stream=None):
     return sims
 
 
-@pytest.mark.parametrize("prec", ["f32", "f64", "bf16"])
+@pytest.mark.parametrize("prec", ["f32", "f64", "bf16", "f16"])
 @pytest.mark.parametrize("steps", [1, 2, 7])
-def test_batch_equals_individual_steps(prec, steps):
+@pytest.mark.parametrize("tile_w", [64, 32])
+def test_batch_equals_individual_steps(prec, steps, tile_w):
     torch = require_gpu()
     stream = torch.cuda.current_stream().cuda_stream
     ws = _members(6, seed=3)
@@ -47,6 +49,8 @@ def test_batch_equals_individual_steps(prec, steps):
     grouped = _make(ws, prec, stream)
     batch = B.Batch(grouped)
     batch.set_stream(stream)
+    batch.set_config(1, 0, 1, tile_w)
+    assert batch.query()["tile_w"] == tile_w
     for s in solo:
         s.step(steps)
     batch.step(steps)
@@ -60,10 +64,11 @@ def test_batch_equals_individual_steps(prec, steps):
 
 @pytest.mark.parametrize("order", [0, 1, 2])
 @pytest.mark.parametrize("split", [0, 1])
-def test_batch_orders_and_graph_replay(order, split):
-    """Every tile order, with the members split into kernel classes (one launch per
-    class: members whose rows start on 16-byte boundaries take the aligned-window
-    sweep) or all through the general sweep; the graph is replayed."""
+@pytest.mark.parametrize("tile_w", [64, 32])
+def test_batch_orders_and_graph_replay(order, split, tile_w):
+    """Every tile order and tile width, with the members split into kernel classes
+    (one launch per class: members whose rows start on 16-byte boundaries take the
+    aligned-window sweep) or all through the general sweep; the graph is replayed."""
     torch = require_gpu()
     stream = torch.cuda.current_stream().cuda_stream
     ws = _members(5, seed=4)
@@ -73,8 +78,9 @@ def test_batch_orders_and_graph_replay(order, split):
     grouped = _make(ws, "f32", stream)
     batch = B.Batch(grouped)
     batch.set_stream(stream)
-    batch.set_config(order, 3, split)
-    assert batch.query()["launches_per_step"] == (2 if split else 1)
+    batch.set_config(order, 3, split, tile_w)
+    q = batch.query()
+    assert q["launches_per_step"] == (2 if split else 1) and q["tile_w"] == tile_w
     for rep in range(3):            # the graph is captured once and replayed
         batch.step(10)
         for s in solo:
@@ -95,10 +101,11 @@ def test_tune_leaves_state_unchanged():
     before = [s.get_populations() for s in sims]
     batch = B.Batch(sims)
     batch.set_stream(stream)
-    order, blocks, split = batch.tune(6)
-    assert order in (0, 1, 2) and blocks in (0, 3, 4) and split in (0, 1)
+    order, blocks, split, tile_w = batch.tune(6)
+    assert order in (0, 1, 2) and blocks in (0, 3, 4) and split in (0, 1) and tile_w in (32, 64)
     q = batch.query()
     assert q["order"] == order and q["blocks_per_sm"] == blocks and q["contexts"] == 4
+    assert q["tile_w"] == tile_w
     for s, f0, w in zip(sims, before, ws):
         fl = ~w["solid"]
         assert s.time() == 3
@@ -134,7 +141,8 @@ def test_batch_requires_same_parity_and_picks_up_changes():
     batch.close()
 
 
-def test_batch_member_matches_oracle_and_d3q19_mix():
+@pytest.mark.parametrize("tile_w", [64, 32])
+def test_batch_member_matches_oracle_and_d3q19_mix(tile_w):
     """A D3Q19 batch mixing the skew-periodic tilted pipe and a sphere box (different
     sizes, alignment and wrap) against the FP64 oracle."""
     require_gpu()
@@ -147,6 +155,7 @@ def test_batch_member_matches_oracle_and_d3q19_mix():
         s.init_equilibrium(rho, u)
         sims.append((s, w, rho, u))
     batch = B.Batch([s for s, *_ in sims])
+    batch.set_config(1, 0, 1, tile_w)
     batch.step(9)
     for s, w, rho, u in sims:
         o = oracle_sim(w)
@@ -157,10 +166,12 @@ def test_batch_member_matches_oracle_and_d3q19_mix():
     batch.close()
 
 
-def test_full_ensemble_batch_equals_one_launch_per_member():
+@pytest.mark.parametrize("tile_w", [None, 32, 64])
+def test_full_ensemble_batch_equals_one_launch_per_member(tile_w):
     """The benchmark's ensemble itself (96 Couette instances from seed 0, n in 48..768,
-    FP32): after tuning and an odd number of graph-replayed steps, every member of
-    the batch holds exactly what stepping it alone gives."""
+    FP32): after tuning (or in a fixed tile width) and an odd number of
+    graph-replayed steps, every member of the batch holds exactly what stepping it
+    alone gives."""
     torch = require_gpu()
     stream = torch.cuda.current_stream().cuda_stream
     ws = [W.ensemble_member(p) for p in W.couette_ensemble(96, 0)]
@@ -173,7 +184,10 @@ def test_full_ensemble_batch_equals_one_launch_per_member():
             lst.append(s)
     batch = B.Batch(grouped)
     batch.set_stream(stream)
-    batch.tune(4)
+    if tile_w is None:
+        batch.tune(4)
+    else:
+        batch.set_config(1, 0, 1, tile_w)
     batch.step(7)
     for s in solo:
         s.step(7)
