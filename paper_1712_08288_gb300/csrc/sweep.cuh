@@ -542,21 +542,29 @@ __device__ __forceinline__ LinkCoef<C> load_coef_nc(const LinkCoef<C> *p) {
   return c;
 }
 
-// resident blocks per SM the register budget is sized for
+// Resident blocks per SM the register budget is sized for (launch bounds).  With
+// 4- and 2-byte storage a block of a single-context sweep takes 44.5 KB (D3Q19),
+// 35.8 KB (D3Q15) or 22.5 KB (D2Q9) of shared memory, so 5, 6 or 9 fit an SM: the
+// register budget follows (96, 80 and 64 registers a thread, 5, 6 and 8 blocks).
+// Batch sweeps keep 96 registers: the members' arguments come from memory and sit in
+// registers, and below 96 they spill, which costs more than the occupancy gains.
 #ifndef LBM_MINBLOCKS_F32
 #define LBM_MINBLOCKS_F32 5
 #endif
 #ifndef LBM_MINBLOCKS_D2Q9
-#define LBM_MINBLOCKS_D2Q9 5
+#define LBM_MINBLOCKS_D2Q9 8
 #endif
-template <class L, class T>
+#ifndef LBM_MINBLOCKS_D3Q15
+#define LBM_MINBLOCKS_D3Q15 6
+#endif
+template <class L, class T, bool BATCH>
 struct MinBlocks {
-  // 4- and 2-byte storage: 5 x 128 threads (up to 96 registers); D2Q9 has fewer
-  // populations per node to keep in registers
-  static constexpr int value = L::Q == 9 ? LBM_MINBLOCKS_D2Q9 : LBM_MINBLOCKS_F32;
+  static constexpr int value = BATCH ? LBM_MINBLOCKS_F32
+                                     : (L::Q == 9 ? LBM_MINBLOCKS_D2Q9
+                                                  : (L::Q == 15 ? LBM_MINBLOCKS_D3Q15 : LBM_MINBLOCKS_F32));
 };
-template <class L>
-struct MinBlocks<L, double> {
+template <class L, bool BATCH>
+struct MinBlocks<L, double, BATCH> {
   static constexpr int value = 4;   // 4 x 128 threads: 128 registers (FP64 arithmetic)
 };
 
@@ -582,7 +590,7 @@ __device__ __forceinline__ const SweepArgs<C> &args_for(const SweepArgs<C> &a, c
 }
 
 template <class L, class T, bool ODD, bool SKEW, bool ALIGNED, class I, bool BATCH, int TW = kTileW>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<L, T>::value)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<L, T, BATCH>::value)
     sweep_kernel(const SweepArgs<typename Storage<T>::C> a, const TileDesc *__restrict__ tiles,
                  int n_tiles, const SweepArgs<typename Storage<T>::C> *__restrict__ inst,
                  const int *__restrict__ tile_inst) {
