@@ -95,6 +95,12 @@ def profiled_fp64_flops():
     return _profile_field(PROFILE_F64, "fp64_flops_per_fluid_node")
 
 
+def profiled_fp64_instructions():
+    """FP64 pipe instructions (DADD + DMUL + DFMA) per fluid-node update of the FP64
+    sweep (same ncu summary)."""
+    return _profile_field(PROFILE_F64, "fp64_instructions_per_fluid_node")
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -287,6 +293,16 @@ def run_gpu(args):
                 line_p["roofline"] = {"bound": "fp64", "flops_per_node": fl_per_node,
                                       "achieved_gflops": round(ach_fl, 1),
                                       "frac_of_fp64_peak": round(ach_fl / fp64_peak, 4)}
+                # the FP64 pipe issues one DADD, DMUL or DFMA per slot: the sweep's FP64
+                # instructions per second against the probe's DFMA issue rate (half its
+                # flop rate)
+                in_per_node = profiled_fp64_instructions()
+                if in_per_node:
+                    ach_in = in_per_node * n_fluid / (lm * 1e-3) / 1e9
+                    line_p["roofline"].update({
+                        "fp64_instructions_per_node": in_per_node,
+                        "achieved_ginst_per_s": round(ach_in, 1),
+                        "frac_of_fp64_issue_rate": round(ach_in / (fp64_peak / 2), 4)})
         prec_lines[prec] = line_p
         del sim
     mlups64 = prec_lines["f64"]["mlups"]
@@ -408,7 +424,8 @@ def summary(line):
     pr = line.get("precisions") or {}
     out = {"frac_hbm": {p: g(pr, p, "frac_of_hbm") for p in ("f32", "bf16", "f16", "f64")},
            "mlups": {p: g(pr, p, "mlups") for p in ("f32", "bf16", "f16", "f64")},
-           "f64_frac_of_fp64_peak": g(pr, "f64", "roofline", "frac_of_fp64_peak")}
+           "f64_frac_of_fp64_peak": g(pr, "f64", "roofline", "frac_of_fp64_peak"),
+           "f64_frac_of_fp64_issue_rate": g(pr, "f64", "roofline", "frac_of_fp64_issue_rate")}
     acc = line.get("accuracy")
     if acc:
         out["pipe_E_r"] = {"L": acc["L"], **{p: ["%.4g" % v for v in acc[p]] for p in ("f64", "f32", "bf16", "f16")}}

@@ -19,11 +19,11 @@
 
 namespace lbm {
 cudaError_t launch_sweep_d2q9(int, bool, const SweepArgs<double> &, const SweepArgs<float> &,
-                              const TileDesc *, int, int, cudaStream_t);
+                               const TileDesc *, int, const TileDesc *, int, cudaStream_t);
 cudaError_t launch_sweep_d3q19(int, bool, const SweepArgs<double> &, const SweepArgs<float> &,
-                               const TileDesc *, int, int, cudaStream_t);
+                               const TileDesc *, int, const TileDesc *, int, cudaStream_t);
 cudaError_t launch_sweep_d3q15(int, bool, const SweepArgs<double> &, const SweepArgs<float> &,
-                               const TileDesc *, int, int, cudaStream_t);
+                               const TileDesc *, int, const TileDesc *, int, cudaStream_t);
 int error_norms_noalloc(int device, int lattice, int precision, const AuxArgs &a, bool odd,
                         const double *u_ref, double *out, cudaStream_t st, const char **why);
 cudaError_t launch_sweep_batch_d2q9(int, int, bool, const void *, const TileDesc *, const int *,
@@ -33,12 +33,12 @@ cudaError_t launch_sweep_batch_d3q19(int, int, bool, const void *, const TileDes
 cudaError_t launch_sweep_batch_d3q15(int, int, bool, const void *, const TileDesc *, const int *,
                                    int, bool, bool, bool, int, cudaStream_t, bool);
 cudaError_t launch_sweep(int lattice, int precision, bool odd, const SweepArgs<double> &a64,
-                         const SweepArgs<float> &a32, const TileDesc *tiles, int n_tiles, int bx,
-                         cudaStream_t st) {
+                         const SweepArgs<float> &a32, const TileDesc *tiles, int n_tiles,
+                         const TileDesc *tiles_half, int n_half, cudaStream_t st) {
   switch (lattice) {
-    case LBM_D2Q9: return launch_sweep_d2q9(precision, odd, a64, a32, tiles, n_tiles, bx, st);
-    case LBM_D3Q15: return launch_sweep_d3q15(precision, odd, a64, a32, tiles, n_tiles, bx, st);
-    default: return launch_sweep_d3q19(precision, odd, a64, a32, tiles, n_tiles, bx, st);
+    case LBM_D2Q9: return launch_sweep_d2q9(precision, odd, a64, a32, tiles, n_tiles, tiles_half, n_half, st);
+    case LBM_D3Q15: return launch_sweep_d3q15(precision, odd, a64, a32, tiles, n_tiles, tiles_half, n_half, st);
+    default: return launch_sweep_d3q19(precision, odd, a64, a32, tiles, n_tiles, tiles_half, n_half, st);
   }
 }
 }  // namespace lbm
@@ -94,9 +94,10 @@ struct lbm_ctx {
   double *u_prev = nullptr;
   double *mom_rho = nullptr;
   double *mom_u = nullptr;
-  TileDesc *tiles = nullptr;    // active tiles of the sweep
+  TileDesc *tiles = nullptr;    // active 64-node tiles of the sweep
   int n_tiles = 0;
-  int bx = 128;                 // tile width = threads per block
+  TileDesc *tiles_half = nullptr;  // the same tiles cut into 32-node halves
+  int n_tiles_half = 0;
 
   // host copy of the cut links in device order (for re-deriving coefficients)
   std::vector<int32_t> link_dir;
@@ -352,6 +353,26 @@ static void free_geometry(lbm_ctx *c) {
   cudaFree(c->lnk); c->lnk = nullptr;
 }
 
+// 64-node tiles cut into 32-node halves; halves without a fluid node are dropped.
+// A half keeps the tile's link-buffer base (its records' offsets are relative to it);
+// the second half's records start after the first half's.  Lanes past a half are
+// marked solid.
+static void half_tiles(const std::vector<TileDesc> &in, std::vector<TileDesc> &out) {
+  constexpr uint64_t kLo = 0xffffffffull;
+  out.clear();
+  out.reserve(2 * in.size());
+  for (const TileDesc &d : in) {
+    TileDesc a = d, h = d;
+    a.solid = d.solid | ~kLo;
+    a.bnd = d.bnd & kLo;
+    h.x0 = d.x0 + 32;
+    h.rb = d.rb + __builtin_popcountll(d.bnd & kLo);
+    h.solid = (d.solid >> 32) | ~kLo;
+    h.bnd = d.bnd >> 32;
+    if ((a.solid & kLo) != kLo) out.push_back(a);
+    if ((h.solid & kLo) != kLo) out.push_back(h);
+  }
+}
 // Tile descriptors (see TileDesc) of every run of kTileW nodes along x that holds
 // at least one fluid node, and the packed records of the boundary nodes, in node
 // order.  solid == nullptr: an all-fluid box without cut links.
@@ -359,8 +380,7 @@ static int upload_tiles(lbm_ctx *c, const uint8_t *solid, const std::vector<uint
                         const std::vector<uint32_t> *bmask, const std::vector<int32_t> *boff) {
   if (c->ny > 65535 || c->nz > 65535)
     return fail(c, LBM_EINVAL, "grid: ny and nz must be below 65536");
-  c->bx = kTileW;   // one warp per tile
-  const int nxb = (c->nx + c->bx - 1) / c->bx;
+  const int nxb = (c->nx + kTileW - 1) / kTileW;
   std::vector<TileDesc> t;
   t.reserve((size_t)nxb * c->ny * c->nz);
   std::vector<uint32_t> rec32;
@@ -369,7 +389,7 @@ static int upload_tiles(lbm_ctx *c, const uint8_t *solid, const std::vector<uint
   for (int z = 0; z < c->nz; ++z)
     for (int y = 0; y < c->ny; ++y)
       for (int xb = 0; xb < nxb; ++xb) {
-        const int x0 = xb * c->bx;
+        const int x0 = xb * kTileW;
         const long long row = (long long)c->nx * (y + (long long)c->ny * z);
         TileDesc d{};
         d.x0 = x0;
@@ -395,6 +415,15 @@ static int upload_tiles(lbm_ctx *c, const uint8_t *solid, const std::vector<uint
   c->n_tiles = (int)t.size();
   cudaFree(c->tiles);
   c->tiles = nullptr;
+  std::vector<TileDesc> th;
+  half_tiles(t, th);
+  c->n_tiles_half = (int)th.size();
+  cudaFree(c->tiles_half);
+  c->tiles_half = nullptr;
+  CUDA_OR_FAIL(c, cudaMalloc((void **)&c->tiles_half, sizeof(TileDesc) * std::max<size_t>(1, th.size())));
+  if (!th.empty())
+    CUDA_OR_FAIL(c, cudaMemcpy(c->tiles_half, th.data(), sizeof(TileDesc) * th.size(),
+                               cudaMemcpyHostToDevice));
   cudaFree(c->rec32);
   c->rec32 = nullptr;
   CUDA_OR_FAIL(c, cudaMalloc((void **)&c->tiles, sizeof(TileDesc) * std::max<size_t>(1, t.size())));
@@ -477,6 +506,8 @@ int lbm_destroy(lbm_ctx *c) {
   adj_ws_free(c);
   cudaFree(c->tiles);
   c->tiles = nullptr;
+  cudaFree(c->tiles_half);
+  c->tiles_half = nullptr;
   cudaFree(c->rec32);
   c->rec32 = nullptr;
   cudaFree(c->partials);
@@ -781,8 +812,8 @@ int lbm_step(lbm_ctx *c, int n) {
       e = launch_two_node(c->lattice, c->precision, c->a64, c->a32, aux_args(c), odd, false, c->tn,
                           c->n_tn, c->tn_delta, c->stream);
     if (e == cudaSuccess)
-      e = launch_sweep(c->lattice, c->precision, odd, c->a64, c->a32, c->tiles, c->n_tiles, c->bx,
-                       c->stream);
+      e = launch_sweep(c->lattice, c->precision, odd, c->a64, c->a32, c->tiles, c->n_tiles,
+                       c->tiles_half, c->n_tiles_half, c->stream);
     if (e == cudaSuccess && c->n_tn)
       e = launch_two_node(c->lattice, c->precision, c->a64, c->a32, aux_args(c), odd, true, c->tn,
                           c->n_tn, c->tn_delta, c->stream);
@@ -1294,26 +1325,6 @@ static bool member_aligned(const lbm_ctx *c) {
   return ((long long)c->nx * store_bytes(c->precision)) % 16 == 0;
 }
 
-// A member's tiles cut into 32-node halves; halves without a fluid node are dropped.
-// A half keeps the tile's link-buffer base (its records' offsets are relative to it);
-// the second half's records start after the first half's.  Lanes past a half are
-// marked solid.
-static void half_tiles(const std::vector<TileDesc> &in, std::vector<TileDesc> &out) {
-  constexpr uint64_t kLo = 0xffffffffull;
-  out.clear();
-  out.reserve(2 * in.size());
-  for (const TileDesc &d : in) {
-    TileDesc a = d, h = d;
-    a.solid = d.solid | ~kLo;
-    a.bnd = d.bnd & kLo;
-    h.x0 = d.x0 + 32;
-    h.rb = d.rb + __builtin_popcountll(d.bnd & kLo);
-    h.solid = (d.solid >> 32) | ~kLo;
-    h.bnd = d.bnd >> 32;
-    if ((a.solid & kLo) != kLo) out.push_back(a);
-    if ((h.solid & kLo) != kLo) out.push_back(h);
-  }
-}
 static int batch_upload(lbm_batch *b) {
   const int n = (int)b->ctx.size();
   b->big = false;

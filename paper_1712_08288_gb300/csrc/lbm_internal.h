@@ -119,9 +119,11 @@ struct SweepArgs {
 };
 
 // launchers (return cudaGetLastError() of the launch)
+// tiles: the 64-node tile list; tiles_half: the same tiles cut into 32-node halves
+// (used by the storage types whose single-context sweep runs half tiles)
 cudaError_t launch_sweep(int lattice, int precision, bool odd, const SweepArgs<double> &a64,
-                         const SweepArgs<float> &a32, const TileDesc *tiles, int n_tiles, int bx,
-                         cudaStream_t st);
+                         const SweepArgs<float> &a32, const TileDesc *tiles, int n_tiles,
+                         const TileDesc *tiles_half, int n_half, cudaStream_t st);
 
 struct AuxArgs {
   void *pop;

@@ -382,20 +382,27 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
 // node after the other.  Every warp owns a private pipeline of kStages shared-memory
 // stages: stage s holds the Q population row windows of one tile (each window up to
 // TW + 16/sizeof(T) elements, start aligned down to 16 bytes), filled by bulk copies
-// that complete on the warp's own mbarrier.  32-node tiles take more stages (3 for
-// 8- and 4-byte storage, 5 for 2-byte storage): a warp keeps most of its bytes in
-// flight while a block still fits the shared memory of the 64-node layout.  Warps
-// never wait for each other.
+// that complete on the warp's own mbarrier.  32-node tiles take more stages with 4-
+// and 2-byte storage (3 and 5): a warp keeps most of its bytes in flight while a
+// block still fits the shared memory of the 64-node layout.  FP64 storage keeps 2
+// stages in 32-node tiles: its sweep is bound by the FP64 pipe, and half the shared
+// memory doubles the blocks per SM (4 instead of 2).  Warps never wait for each other.
 constexpr int kWarpsPerBlock = 4;
 
 #ifndef LBM_STAGES_4B
 #define LBM_STAGES_4B 2
 #endif
+#ifndef LBM_STAGES_8B
+#define LBM_STAGES_8B 2
+#endif
+#ifndef LBM_STAGES_8B_32
+#define LBM_STAGES_8B_32 2
+#endif
 template <class T, int TW = kTileW>
 struct StageShape {
   static_assert(TW == 32 || TW == 64, "tiles are one or two nodes per lane wide");
-  static constexpr int kStages = TW == 64 ? (sizeof(T) == 8 ? 2 : (sizeof(T) == 4 ? LBM_STAGES_4B : 3))
-                                          : (sizeof(T) == 2 ? 5 : 3);
+  static constexpr int kStages = TW == 64 ? (sizeof(T) == 8 ? LBM_STAGES_8B : (sizeof(T) == 4 ? LBM_STAGES_4B : 3))
+                                          : (sizeof(T) == 2 ? 5 : (sizeof(T) == 8 ? LBM_STAGES_8B_32 : 3));
   static constexpr int kWidth = TW + 16 / (int)sizeof(T);   // elements per window
   static constexpr int kRecs = TW + 4;                       // record window (uint32)
 };
@@ -833,19 +840,30 @@ void launch_persistent(const A &a, const TileDesc *tiles, int n_tiles, size_t sm
   if (!prepare_only) Kernel<<<grid, threads, smem, st>>>(a, tiles, n_tiles, inst, tile_inst);
 }
 
+// Tile width of the single-context sweep per storage type: 64 nodes, or 32-node
+// half tiles for FP64 storage (see StageShape; on the L = 256 pipe 3.99 instead of
+// 4.01 ms per step, the same with 64-node tiles in one stage or 32-node tiles in 3).
+#ifndef LBM_TILEW_F64
+#define LBM_TILEW_F64 32
+#endif
+template <class T>
+constexpr int single_tile_w() { return sizeof(T) == 8 ? LBM_TILEW_F64 : kTileW; }
+
 template <class L, class T>
-cudaError_t launch_sweep_t(bool odd, const SweepArgs<typename Storage<T>::C> &a, const TileDesc *tiles,
-                           int n_tiles, int bx, cudaStream_t st) {
+cudaError_t launch_sweep_t(bool odd, const SweepArgs<typename Storage<T>::C> &a, const TileDesc *tiles64,
+                           int n_tiles64, const TileDesc *tiles_half, int n_half, cudaStream_t st) {
+  constexpr int TW = single_tile_w<T>();
+  const TileDesc *tiles = TW == kTileW ? tiles64 : tiles_half;
+  const int n_tiles = TW == kTileW ? n_tiles64 : n_half;
   if (n_tiles == 0) return cudaSuccess;
   const bool skew = a.sy != 0 || a.sz != 0;
   const bool big = (long long)L::Q * a.S >= (1LL << 31);
-  const size_t smem = kWarpsPerBlock * warp_smem_bytes<L, T>();
-  (void)bx;
+  const size_t smem = kWarpsPerBlock * warp_smem_bytes<L, T, TW>();
   const bool aligned = ((long long)a.nx * (long long)sizeof(T)) % 16 == 0;
-#define LBM_LAUNCH(O, S, I)                                                              \
-  do {                                                                                   \
-    if (aligned) launch_persistent<sweep_kernel<L, T, O, S, true, I, false>>(a, tiles, n_tiles, smem, st);   \
-    else launch_persistent<sweep_kernel<L, T, O, S, false, I, false>>(a, tiles, n_tiles, smem, st);         \
+#define LBM_LAUNCH(O, S, I)                                                                              \
+  do {                                                                                                   \
+    if (aligned) launch_persistent<sweep_kernel<L, T, O, S, true, I, false, TW>>(a, tiles, n_tiles, smem, st);  \
+    else launch_persistent<sweep_kernel<L, T, O, S, false, I, false, TW>>(a, tiles, n_tiles, smem, st);        \
   } while (0)
   if (big) {
     if (odd) { if (skew) LBM_LAUNCH(true, true, long long); else LBM_LAUNCH(true, false, long long); }

@@ -7,12 +7,12 @@ namespace lbm {
 
 cudaError_t launch_sweep_d3q15(int precision, bool odd, const SweepArgs<double> &a64,
                            const SweepArgs<float> &a32, const TileDesc *tiles, int n_tiles,
-                           int bx, cudaStream_t st) {
+                           const TileDesc *tiles_half, int n_half, cudaStream_t st) {
   switch (precision) {
-    case 0: return launch_sweep_t<D3Q15, double>(odd, a64, tiles, n_tiles, bx, st);
-    case 1: return launch_sweep_t<D3Q15, float>(odd, a32, tiles, n_tiles, bx, st);
-    case 2: return launch_sweep_t<D3Q15, __nv_bfloat16>(odd, a32, tiles, n_tiles, bx, st);
-    case 3: return launch_sweep_t<D3Q15, __half>(odd, a32, tiles, n_tiles, bx, st);
+    case 0: return launch_sweep_t<D3Q15, double>(odd, a64, tiles, n_tiles, tiles_half, n_half, st);
+    case 1: return launch_sweep_t<D3Q15, float>(odd, a32, tiles, n_tiles, tiles_half, n_half, st);
+    case 2: return launch_sweep_t<D3Q15, __nv_bfloat16>(odd, a32, tiles, n_tiles, tiles_half, n_half, st);
+    case 3: return launch_sweep_t<D3Q15, __half>(odd, a32, tiles, n_tiles, tiles_half, n_half, st);
     default: return cudaErrorInvalidValue;
   }
 }
