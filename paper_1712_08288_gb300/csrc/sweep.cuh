@@ -182,17 +182,23 @@ __device__ __forceinline__ void collide_d3q19(const C (&g)[19], C (&gp)[19], con
   ev[6] = Pxz - r[15];
   ev[7] = Pyz + r[14];
   ev[8] = Pyz - r[14];
-  // odd parts minus the force term of the pair's first direction
+  // odd parts minus the force term of the pair's first direction: with the force
+  // folded into the flux rates (ra = r_a - F_a) the edge pairs share the sums
+  // (ra + r16), (rb - r17), ... of their two directions
   const C F0 = a.F[0], F1 = a.F[1], F2 = a.F[2];
-  od[0] = C(-4) * r[4] - F0;
-  od[1] = C(-4) * r[6] - F1;
-  od[2] = C(-4) * r[8] - F2;
-  od[3] = r[4] + r[6] + r[16] - r[17] - (F0 + F1);
-  od[4] = r[4] - r[6] + r[16] + r[17] - (F0 - F1);
-  od[5] = r[4] + r[8] - r[16] + r[18] - (F0 + F2);
-  od[6] = r[4] - r[8] - r[16] - r[18] - (F0 - F2);
-  od[7] = r[6] + r[8] + r[17] - r[18] - (F1 + F2);
-  od[8] = r[6] - r[8] + r[17] + r[18] - (F1 - F2);
+  const C rx = r[4] - F0, ry = r[6] - F1, rz = r[8] - F2;
+  od[0] = C(-4) * rx - C(5) * F0;
+  od[1] = C(-4) * ry - C(5) * F1;
+  od[2] = C(-4) * rz - C(5) * F2;
+  const C xa = rx + r[16], ya = ry - r[17];
+  od[3] = xa + ya;
+  od[4] = xa - ya;
+  const C xb = rx - r[16], zb = rz + r[18];
+  od[5] = xb + zb;
+  od[6] = xb - zb;
+  const C yc = ry + r[17], zc = rz - r[18];
+  od[7] = yc + zc;
+  od[8] = yc - zc;
   gp[0] = g[0] - (C(-30) * r[1] + C(12) * r[2]);
 #pragma unroll
   for (int p = 0; p < 9; ++p) {
@@ -564,11 +570,16 @@ __device__ __forceinline__ LinkCoef<C> load_coef_nc(const LinkCoef<C> *p) {
 #ifndef LBM_MINBLOCKS_D3Q15
 #define LBM_MINBLOCKS_D3Q15 6
 #endif
+#ifndef LBM_MINBLOCKS_D3Q19_2B
+#define LBM_MINBLOCKS_D3Q19_2B 5
+#endif
 template <class L, class T, bool BATCH>
 struct MinBlocks {
-  static constexpr int value = BATCH ? LBM_MINBLOCKS_F32
-                                     : (L::Q == 9 ? LBM_MINBLOCKS_D2Q9
-                                                  : (L::Q == 15 ? LBM_MINBLOCKS_D3Q15 : LBM_MINBLOCKS_F32));
+  static constexpr int value =
+      BATCH ? LBM_MINBLOCKS_F32
+            : (L::Q == 9 ? LBM_MINBLOCKS_D2Q9
+                         : (L::Q == 15 ? LBM_MINBLOCKS_D3Q15
+                                       : (sizeof(T) == 2 ? LBM_MINBLOCKS_D3Q19_2B : LBM_MINBLOCKS_F32)));
 };
 template <class L, bool BATCH>
 struct MinBlocks<L, double, BATCH> {
@@ -846,8 +857,16 @@ void launch_persistent(const A &a, const TileDesc *tiles, int n_tiles, size_t sm
 #ifndef LBM_TILEW_F64
 #define LBM_TILEW_F64 32
 #endif
+#ifndef LBM_TILEW_4B
+#define LBM_TILEW_4B 64
+#endif
+#ifndef LBM_TILEW_2B
+#define LBM_TILEW_2B 64
+#endif
 template <class T>
-constexpr int single_tile_w() { return sizeof(T) == 8 ? LBM_TILEW_F64 : kTileW; }
+constexpr int single_tile_w() {
+  return sizeof(T) == 8 ? LBM_TILEW_F64 : (sizeof(T) == 4 ? LBM_TILEW_4B : LBM_TILEW_2B);
+}
 
 template <class L, class T>
 cudaError_t launch_sweep_t(bool odd, const SweepArgs<typename Storage<T>::C> &a, const TileDesc *tiles64,
