@@ -559,8 +559,11 @@ __device__ __forceinline__ LinkCoef<C> load_coef_nc(const LinkCoef<C> *p) {
 // 4- and 2-byte storage a block of a single-context sweep takes 44.5 KB (D3Q19),
 // 35.8 KB (D3Q15) or 22.5 KB (D2Q9) of shared memory, so 5, 6 or 9 fit an SM: the
 // register budget follows (96, 80 and 64 registers a thread, 5, 6 and 8 blocks).
-// Batch sweeps keep 96 registers: the members' arguments come from memory and sit in
-// registers, and below 96 they spill, which costs more than the occupancy gains.
+// Batch sweeps read their members' arguments from memory into registers: D2Q9 keeps
+// 96 registers (below that it spills, which costs more than the occupancy gains), the
+// 3D lattices take 128 (4 blocks): with 96 they spill 40-200 bytes a thread, and a
+// D3Q19 batch of tilted pipes runs 9 % faster at 4 blocks without spills than at 5
+// with them.
 #ifndef LBM_MINBLOCKS_F32
 #define LBM_MINBLOCKS_F32 5
 #endif
@@ -573,17 +576,26 @@ __device__ __forceinline__ LinkCoef<C> load_coef_nc(const LinkCoef<C> *p) {
 #ifndef LBM_MINBLOCKS_D3Q19_2B
 #define LBM_MINBLOCKS_D3Q19_2B 5
 #endif
+#ifndef LBM_MINBLOCKS_BATCH_3D
+#define LBM_MINBLOCKS_BATCH_3D 4
+#endif
 template <class L, class T, bool BATCH>
 struct MinBlocks {
   static constexpr int value =
-      BATCH ? LBM_MINBLOCKS_F32
+      BATCH ? (L::Q == 9 ? LBM_MINBLOCKS_F32 : LBM_MINBLOCKS_BATCH_3D)
             : (L::Q == 9 ? LBM_MINBLOCKS_D2Q9
                          : (L::Q == 15 ? LBM_MINBLOCKS_D3Q15
                                        : (sizeof(T) == 2 ? LBM_MINBLOCKS_D3Q19_2B : LBM_MINBLOCKS_F32)));
 };
+#ifndef LBM_MINBLOCKS_BATCH_F64
+#define LBM_MINBLOCKS_BATCH_F64 2
+#endif
 template <class L, bool BATCH>
 struct MinBlocks<L, double, BATCH> {
-  static constexpr int value = 4;   // 4 x 128 threads: 128 registers (FP64 arithmetic)
+  // 4 x 128 threads: 128 registers (FP64 arithmetic).  Batches: 2 (the members'
+  // arguments on top of the FP64 state spill 60-180 bytes a thread at 128 or 168
+  // registers; 64-node FP64 tiles fit only 2 blocks' shared memory anyway)
+  static constexpr int value = BATCH ? LBM_MINBLOCKS_BATCH_F64 : 4;
 };
 
 // One fused time step.  Persistent warps: global warp w handles tiles

@@ -282,6 +282,11 @@ def test_other_collision_operators_through_the_same_sweep(kind):
     ("D3Q19", (2, 5, 4), (0, 0), "f32"),
     ("D3Q15", (1, 4, 4), (1, 3), "f64"),
     ("D3Q19", (65, 4, 3), (0, 0), "f64"),   # a full tile plus a one-node tile per row
+    # FP64 sweeps run 32-node half tiles: the x = nx-1 edge in the second half, in the
+    # only half (both edges in one tile), and a ragged one-node half, with skew
+    ("D3Q19", (40, 5, 4), (1, 2), "f64"),
+    ("D3Q19", (24, 4, 5), (2, 1), "f64"),
+    ("D2Q9", (33, 6, 1), (0, 0), "f64"),
 ])
 def test_thin_and_degenerate_grids(lattice, shape, skew, prec):
     """Grids one or two nodes thick, a single row, and a ragged last tile: walls on the
