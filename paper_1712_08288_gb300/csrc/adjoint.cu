@@ -207,104 +207,6 @@ __device__ __forceinline__ void moments_all(const C (&v)[L::Q], C (&m)[L::Q]) {
   }
 }
 
-// D3Q19 moments m = M v and the transpose product out = M^T nu with the sums shared
-// as in the factored collision: pair sums s_p and differences d_p, the face and
-// edge sums (rho, e, eps), the plane sums (the second-order rows), the fluxes
-// (q_a = j_a - 5 d_a); the transpose shares the face, edge and plane parts.  Used by
-// the FP64 adjoint step, which is bound by the FP64 pipe.
-template <class C>
-LBM_HD constexpr void moments_d3q19(const C (&v)[19], C (&m)[19]) {
-  C s[9] = {}, d[9] = {};
-  for (int p = 0; p < 9; ++p) {
-    s[p] = v[2 * p + 1] + v[2 * p + 2];
-    d[p] = v[2 * p + 1] - v[2 * p + 2];
-  }
-  const C F = s[0] + s[1] + s[2];
-  const C Exy = s[3] + s[4], Exz = s[5] + s[6], Eyz = s[7] + s[8];
-  const C E = Exy + Exz + Eyz;
-  const C jx = d[0] + d[3] + d[4] + d[5] + d[6];
-  const C jy = d[1] + d[3] - d[4] + d[7] + d[8];
-  const C jz = d[2] + d[5] - d[6] + d[7] - d[8];
-  const C Exyz = Exy + Exz - C(2) * Eyz;
-  const C Wxy = Exy - Exz;
-  m[0] = v[0] + F + E;
-  m[1] = C(-30) * v[0] - C(11) * F + C(8) * E;
-  m[2] = C(12) * v[0] - C(4) * F + E;
-  m[3] = jx;
-  m[4] = jx - C(5) * d[0];
-  m[5] = jy;
-  m[6] = jy - C(5) * d[1];
-  m[7] = jz;
-  m[8] = jz - C(5) * d[2];
-  m[9] = C(2) * s[0] - s[1] - s[2] + Exyz;
-  m[10] = C(-4) * s[0] + C(2) * (s[1] + s[2]) + Exyz;
-  m[11] = s[1] - s[2] + Wxy;
-  m[12] = C(2) * (s[2] - s[1]) + Wxy;
-  m[13] = s[3] - s[4];
-  m[14] = s[7] - s[8];
-  m[15] = s[5] - s[6];
-  m[16] = d[3] + d[4] - d[5] - d[6];
-  m[17] = d[4] - d[3] + d[7] + d[8];
-  m[18] = d[5] - d[6] - d[7] + d[8];
-}
-template <class C>
-LBM_HD constexpr void mt_d3q19(const C (&nu)[19], C (&out)[19]) {
-  // even parts per pair: rows rho, e, eps (faces Cf, edges Ce) and the plane rows
-  const C Cf = nu[0] - C(11) * nu[1] - C(4) * nu[2];
-  const C Ce = nu[0] + C(8) * nu[1] + nu[2];
-  const C A = nu[9] + nu[10], B = nu[11] + nu[12];
-  const C Y = Cf - nu[9] + C(2) * nu[10], Z = nu[11] - C(2) * nu[12];
-  const C Pxy = Ce + A + B, Pxz = Ce + A - B, Pyz = Ce - C(2) * A;
-  C ev[9] = {}, od[9] = {};
-  ev[0] = Cf + C(2) * nu[9] - C(4) * nu[10];
-  ev[1] = Y + Z;
-  ev[2] = Y - Z;
-  ev[3] = Pxy + nu[13];
-  ev[4] = Pxy - nu[13];
-  ev[5] = Pxz + nu[15];
-  ev[6] = Pxz - nu[15];
-  ev[7] = Pyz + nu[14];
-  ev[8] = Pyz - nu[14];
-  // odd parts: j_a and q_a rows (faces: j_a - 4 q_a, edges: j_a + q_a) and m_x,y,z
-  od[0] = nu[3] - C(4) * nu[4];
-  od[1] = nu[5] - C(4) * nu[6];
-  od[2] = nu[7] - C(4) * nu[8];
-  const C rx = nu[3] + nu[4], ry = nu[5] + nu[6], rz = nu[7] + nu[8];
-  const C xa = rx + nu[16], ya = ry - nu[17];
-  od[3] = xa + ya;
-  od[4] = xa - ya;
-  const C xb = rx - nu[16], zb = rz + nu[18];
-  od[5] = xb + zb;
-  od[6] = xb - zb;
-  const C yc = ry + nu[17], zc = rz - nu[18];
-  od[7] = yc + zc;
-  od[8] = yc - zc;
-  out[0] = nu[0] - C(30) * nu[1] + C(12) * nu[2];
-  for (int p = 0; p < 9; ++p) {
-    out[2 * p + 1] = ev[p] + od[p];
-    out[2 * p + 2] = ev[p] - od[p];
-  }
-}
-// both against the lattice's M, entry by entry, at compile time
-constexpr bool factored_d3q19_matches_M() {
-  for (int i = 0; i < 19; ++i) {
-    int v[19] = {}, m[19] = {};
-    v[i] = 1;
-    moments_d3q19<int>(v, m);
-    for (int k = 0; k < 19; ++k)
-      if (m[k] != D3Q19::M(k, i)) return false;
-  }
-  for (int k = 0; k < 19; ++k) {
-    int nu[19] = {}, out[19] = {};
-    nu[k] = 1;
-    mt_d3q19<int>(nu, out);
-    for (int i = 0; i < 19; ++i)
-      if (out[i] != D3Q19::M(k, i)) return false;
-  }
-  return true;
-}
-static_assert(factored_d3q19_matches_M(), "factored D3Q19 moments / transpose differ from M");
-
 // One step back in time, one node per thread.  SMALL: node indices fit in 31 bits,
 // so neighbour indices come from the node's wrapped coordinates in 32-bit
 // arithmetic.
@@ -391,11 +293,12 @@ __global__ void __launch_bounds__(kAdjThreads, sizeof(C) == 4 ? LBM_ADJ_MINB_F32
       }
     }
     // collision transpose in moment space
-    constexpr bool kFactored = std::is_same_v<L, D3Q19> && sizeof(C) == 8;
+    // FP64: the factored forms (the FP64 pipe bounds the step)
+    constexpr bool kFactored = sizeof(C) == 8;
     C m[Q], mu[Q];
     if constexpr (kFactored) {
-      moments_d3q19<C>(g, m);
-      moments_d3q19<C>(lp, mu);
+      fmoments<C>(L{}, g, m);
+      fmoments<C>(L{}, lp, mu);
     } else {
       moments_all<L, C>(g, m);
       moments_all<L, C>(lp, mu);
@@ -423,7 +326,7 @@ __global__ void __launch_bounds__(kAdjThreads, sizeof(C) == 4 ? LBM_ADJ_MINB_F32
     // lambda(t) = M^T nu + boundary terms, pair form
     if constexpr (kFactored) {
       C t[Q];
-      mt_d3q19<C>(nu, t);
+      fmt<true, C>(L{}, nu, t);
 #pragma unroll
       for (int i = 0; i < Q; ++i) lam_out[(long long)i * N + n] = lpre[i] + t[i];
     } else {

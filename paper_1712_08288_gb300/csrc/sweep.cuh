@@ -207,6 +207,227 @@ __device__ __forceinline__ void collide_d3q19(const C (&g)[19], C (&gp)[19], con
   }
 }
 
+// Factored moment transforms per lattice: m = M v (fmoments) and out = M^T nu (fmt)
+// with the sums shared: pair sums s_p and differences d_p, the sums over faces,
+// edges or corners (rho, e, eps), the plane sums (the second-order rows), the fluxes
+// q_a from j_a and the face differences.  fmt<false> leaves out row 0 (rho), which a
+// collision never relaxes.  factored_matches_M<L>() compares both with the lattice's M
+// entry by entry; the static_asserts below run it at compile time.
+template <class C>
+LBM_HD constexpr void fmoments(D2Q9, const C (&v)[9], C (&m)[9]) {
+  // pairs (1,3), (2,4) faces, (5,7), (6,8) diagonals
+  const C s0 = v[1] + v[3], s1 = v[2] + v[4], s2 = v[5] + v[7], s3 = v[6] + v[8];
+  const C d0 = v[1] - v[3], d1 = v[2] - v[4], d2 = v[5] - v[7], d3 = v[6] - v[8];
+  const C F = s0 + s1, E = s2 + s3;
+  const C jx = d0 + d2 - d3, jy = d1 + d2 + d3;
+  m[0] = v[0] + F + E;
+  m[1] = C(-4) * v[0] - F + C(2) * E;
+  m[2] = C(4) * v[0] - C(2) * F + E;
+  m[3] = jx;
+  m[4] = jx - C(3) * d0;
+  m[5] = jy;
+  m[6] = jy - C(3) * d1;
+  m[7] = s0 - s1;
+  m[8] = s2 - s3;
+}
+template <bool kRho, class C>
+LBM_HD constexpr void fmt(D2Q9, const C (&nu)[9], C (&out)[9]) {
+  const C Cf = kRho ? nu[0] - nu[1] - C(2) * nu[2] : -nu[1] - C(2) * nu[2];
+  const C Ce = kRho ? nu[0] + C(2) * nu[1] + nu[2] : C(2) * nu[1] + nu[2];
+  const C X = nu[3] + nu[4], Y = nu[5] + nu[6];
+  const C ev0 = Cf + nu[7], ev1 = Cf - nu[7], ev2 = Ce + nu[8], ev3 = Ce - nu[8];
+  const C od0 = nu[3] - C(2) * nu[4], od1 = nu[5] - C(2) * nu[6], od2 = X + Y, od3 = Y - X;
+  out[0] = kRho ? nu[0] - C(4) * nu[1] + C(4) * nu[2] : C(-4) * nu[1] + C(4) * nu[2];
+  out[1] = ev0 + od0;
+  out[3] = ev0 - od0;
+  out[2] = ev1 + od1;
+  out[4] = ev1 - od1;
+  out[5] = ev2 + od2;
+  out[7] = ev2 - od2;
+  out[6] = ev3 + od3;
+  out[8] = ev3 - od3;
+}
+
+template <class C>
+LBM_HD constexpr void fmoments(D3Q15, const C (&v)[15], C (&m)[15]) {
+  // pairs (1,2), (3,4), (5,6) faces, (7,14), (8,13), (9,12), (10,11) corners
+  const C s0 = v[1] + v[2], s1 = v[3] + v[4], s2 = v[5] + v[6];
+  const C d0 = v[1] - v[2], d1 = v[3] - v[4], d2 = v[5] - v[6];
+  const C s3 = v[7] + v[14], s4 = v[8] + v[13], s5 = v[9] + v[12], s6 = v[10] + v[11];
+  const C d3 = v[7] - v[14], d4 = v[8] - v[13], d5 = v[9] - v[12], d6 = v[10] - v[11];
+  const C F = s0 + s1 + s2;
+  const C ca = s3 + s6, cb = s4 + s5, cc = s3 - s6, cd = s4 - s5;
+  const C ce = d3 + d6, cf = d4 + d5, cg = d3 - d6, ch = d4 - d5;
+  const C K = ca + cb;
+  const C jx = d0 + cg - ch, jy = d1 + cg + ch, jz = d2 + ce + cf;
+  m[0] = v[0] + F + K;
+  m[1] = C(-2) * v[0] - F + K;
+  m[2] = C(16) * v[0] - C(4) * F + K;
+  m[3] = jx;
+  m[4] = jx - C(5) * d0;
+  m[5] = jy;
+  m[6] = jy - C(5) * d1;
+  m[7] = jz;
+  m[8] = jz - C(5) * d2;
+  m[9] = C(2) * s0 - s1 - s2;
+  m[10] = s1 - s2;
+  m[11] = ca - cb;
+  m[12] = cc + cd;
+  m[13] = cc - cd;
+  m[14] = ce - cf;
+}
+template <bool kRho, class C>
+LBM_HD constexpr void fmt(D3Q15, const C (&nu)[15], C (&out)[15]) {
+  const C Cf = kRho ? nu[0] - nu[1] - C(4) * nu[2] : -nu[1] - C(4) * nu[2];
+  const C Cc = kRho ? nu[0] + nu[1] + nu[2] : nu[1] + nu[2];
+  const C ev0 = Cf + C(2) * nu[9], ev1 = Cf - nu[9] + nu[10], ev2 = Cf - nu[9] - nu[10];
+  const C od0 = nu[3] - C(4) * nu[4], od1 = nu[5] - C(4) * nu[6], od2 = nu[7] - C(4) * nu[8];
+  const C P = Cc + nu[12], Qm = Cc - nu[12], A = nu[11] + nu[13], B = nu[11] - nu[13];
+  const C X = nu[3] + nu[4], Y = nu[5] + nu[6], Z = nu[7] + nu[8];
+  const C YZp = Y + Z, YZm = Z - Y, Xp = X + nu[14], Xm = X - nu[14];
+  out[0] = kRho ? nu[0] - C(2) * nu[1] + C(16) * nu[2] : C(-2) * nu[1] + C(16) * nu[2];
+  out[1] = ev0 + od0;
+  out[2] = ev0 - od0;
+  out[3] = ev1 + od1;
+  out[4] = ev1 - od1;
+  out[5] = ev2 + od2;
+  out[6] = ev2 - od2;
+  out[7] = (P + A) + (YZp + Xp);
+  out[14] = (P + A) - (YZp + Xp);
+  out[8] = (P - A) + (YZp - Xp);
+  out[13] = (P - A) - (YZp - Xp);
+  out[9] = (Qm - B) + (YZm + Xm);
+  out[12] = (Qm - B) - (YZm + Xm);
+  out[10] = (Qm + B) + (YZm - Xm);
+  out[11] = (Qm + B) - (YZm - Xm);
+}
+
+template <class C>
+LBM_HD constexpr void fmoments(D3Q19, const C (&v)[19], C (&m)[19]) {
+  // pairs (2p+1, 2p+2): faces p = 0..2, edges p = 3..8 (xy, xy, xz, xz, yz, yz)
+  C s[9] = {}, d[9] = {};
+  for (int p = 0; p < 9; ++p) {
+    s[p] = v[2 * p + 1] + v[2 * p + 2];
+    d[p] = v[2 * p + 1] - v[2 * p + 2];
+  }
+  const C F = s[0] + s[1] + s[2];
+  const C Exy = s[3] + s[4], Exz = s[5] + s[6], Eyz = s[7] + s[8];
+  const C E = Exy + Exz + Eyz;
+  const C jx = d[0] + d[3] + d[4] + d[5] + d[6];
+  const C jy = d[1] + d[3] - d[4] + d[7] + d[8];
+  const C jz = d[2] + d[5] - d[6] + d[7] - d[8];
+  const C Exyz = Exy + Exz - C(2) * Eyz;
+  const C Wxy = Exy - Exz;
+  m[0] = v[0] + F + E;
+  m[1] = C(-30) * v[0] - C(11) * F + C(8) * E;
+  m[2] = C(12) * v[0] - C(4) * F + E;
+  m[3] = jx;
+  m[4] = jx - C(5) * d[0];
+  m[5] = jy;
+  m[6] = jy - C(5) * d[1];
+  m[7] = jz;
+  m[8] = jz - C(5) * d[2];
+  m[9] = C(2) * s[0] - s[1] - s[2] + Exyz;
+  m[10] = C(-4) * s[0] + C(2) * (s[1] + s[2]) + Exyz;
+  m[11] = s[1] - s[2] + Wxy;
+  m[12] = C(2) * (s[2] - s[1]) + Wxy;
+  m[13] = s[3] - s[4];
+  m[14] = s[7] - s[8];
+  m[15] = s[5] - s[6];
+  m[16] = d[3] + d[4] - d[5] - d[6];
+  m[17] = d[4] - d[3] + d[7] + d[8];
+  m[18] = d[5] - d[6] - d[7] + d[8];
+}
+template <bool kRho, class C>
+LBM_HD constexpr void fmt(D3Q19, const C (&nu)[19], C (&out)[19]) {
+  // even parts per pair: rows rho, e, eps (faces Cf, edges Ce) and the plane rows
+  const C Cf = kRho ? nu[0] - C(11) * nu[1] - C(4) * nu[2] : C(-11) * nu[1] - C(4) * nu[2];
+  const C Ce = kRho ? nu[0] + C(8) * nu[1] + nu[2] : C(8) * nu[1] + nu[2];
+  const C A = nu[9] + nu[10], B = nu[11] + nu[12];
+  const C Y = Cf - nu[9] + C(2) * nu[10], Z = nu[11] - C(2) * nu[12];
+  const C Pxy = Ce + A + B, Pxz = Ce + A - B, Pyz = Ce - C(2) * A;
+  C ev[9] = {}, od[9] = {};
+  ev[0] = Cf + C(2) * nu[9] - C(4) * nu[10];
+  ev[1] = Y + Z;
+  ev[2] = Y - Z;
+  ev[3] = Pxy + nu[13];
+  ev[4] = Pxy - nu[13];
+  ev[5] = Pxz + nu[15];
+  ev[6] = Pxz - nu[15];
+  ev[7] = Pyz + nu[14];
+  ev[8] = Pyz - nu[14];
+  // odd parts: j_a and q_a rows (faces: j_a - 4 q_a, edges: j_a + q_a) and m_x,y,z
+  od[0] = nu[3] - C(4) * nu[4];
+  od[1] = nu[5] - C(4) * nu[6];
+  od[2] = nu[7] - C(4) * nu[8];
+  const C rx = nu[3] + nu[4], ry = nu[5] + nu[6], rz = nu[7] + nu[8];
+  const C xa = rx + nu[16], ya = ry - nu[17];
+  od[3] = xa + ya;
+  od[4] = xa - ya;
+  const C xb = rx - nu[16], zb = rz + nu[18];
+  od[5] = xb + zb;
+  od[6] = xb - zb;
+  const C yc = ry + nu[17], zc = rz - nu[18];
+  od[7] = yc + zc;
+  od[8] = yc - zc;
+  out[0] = kRho ? nu[0] - C(30) * nu[1] + C(12) * nu[2] : C(-30) * nu[1] + C(12) * nu[2];
+  for (int p = 0; p < 9; ++p) {
+    out[2 * p + 1] = ev[p] + od[p];
+    out[2 * p + 2] = ev[p] - od[p];
+  }
+}
+
+template <class L>
+constexpr bool factored_matches_M() {
+  constexpr int Q = L::Q;
+  for (int i = 0; i < Q; ++i) {
+    int v[Q] = {}, m[Q] = {};
+    v[i] = 1;
+    fmoments<int>(L{}, v, m);
+    for (int k = 0; k < Q; ++k)
+      if (m[k] != L::M(k, i)) return false;
+  }
+  for (int k = 0; k < Q; ++k) {
+    int nu[Q] = {}, out[Q] = {}, out0[Q] = {};
+    nu[k] = 1;
+    fmt<true, int>(L{}, nu, out);
+    fmt<false, int>(L{}, nu, out0);
+    for (int i = 0; i < Q; ++i) {
+      if (out[i] != L::M(k, i)) return false;
+      if (out0[i] != (k == 0 ? 0 : L::M(k, i))) return false;
+    }
+  }
+  return true;
+}
+static_assert(factored_matches_M<D2Q9>(), "factored D2Q9 transforms differ from M");
+static_assert(factored_matches_M<D3Q15>(), "factored D3Q15 transforms differ from M");
+static_assert(factored_matches_M<D3Q19>(), "factored D3Q19 transforms differ from M");
+
+// MRT collision through the factored transforms (D2Q9, D3Q15): r_k = s_k (m_k - m^eq_k)
+// / |M_k|^2 on the relaxed rows, r = -F on the momentum rows (the force term), and
+// g' = g - M^T r.
+template <class L, class C>
+__device__ __forceinline__ void collide_factored(const C (&g)[L::Q], C (&gp)[L::Q], const SweepArgs<C> &a,
+                                                 C &drho_out) {
+  constexpr int Q = L::Q;
+  C m[Q];
+  fmoments<C>(L{}, g, m);
+  const C drho = m[0], jx = m[3], jy = m[5], jz = L::D == 3 ? m[7] : C(0);
+  drho_out = drho;
+  const C ir0 = a.inv_rho0;
+  C r[Q];
+#pragma unroll
+  for (int k = 0; k < Q; ++k)
+    r[k] = Rows<L>::cons(k) ? C(0) : a.sn[k] * (m[k] - meq(L{}, k, drho, jx, jy, jz, ir0));
+  r[3] = -a.F[0];
+  r[5] = -a.F[1];
+  if constexpr (L::D == 3) r[7] = -a.F[2];
+  C t[Q];
+  fmt<false, C>(L{}, r, t);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) gp[i] = g[i] - t[i];
+}
+
 // MRT collision with the body force, deviation variables, g -> gp.  T is the
 // storage type (it selects the form of the D3Q19 collision).
 template <class L, class C, class T = C>
@@ -220,6 +441,10 @@ __device__ __forceinline__ void collide(const C (&g)[L::Q], C (&gp)[L::Q], const
     // tracks FP64 closer (E_r 0.2 % from FP64 after 20000 steps, against 2.3 % with
     // the factored form).
     collide_d3q19<C>(g, gp, a, drho_out);
+    return;
+  } else if constexpr (!std::is_same_v<L, D3Q19> && (sizeof(C) == 8 || sizeof(T) == 2)) {
+    // D2Q9 and D3Q15 likewise
+    collide_factored<L, C>(g, gp, a, drho_out);
     return;
   }
   constexpr int Q = L::Q;
