@@ -373,6 +373,7 @@ static void half_tiles(const std::vector<TileDesc> &in, std::vector<TileDesc> &o
     if ((h.solid & kLo) != kLo) out.push_back(h);
   }
 }
+
 // Tile descriptors (see TileDesc) of every run of kTileW nodes along x that holds
 // at least one fluid node, and the packed records of the boundary nodes, in node
 // order.  solid == nullptr: an all-fluid box without cut links.
