@@ -607,9 +607,9 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
       : "memory");
 }
 
-// Work decomposition.  A tile is a run of TW nodes along x (TW = kTileW = 64 for a
-// single context; batches may take 32) that holds at least one fluid node; tiles
-// are listed once per geometry.  A warp processes a tile TW/32 nodes per lane, one
+// Work decomposition.  A tile is a run of TW nodes along x (TW = kTileW = 64, or
+// 32-node half tiles: the single-context FP64 sweep and, by choice, batches) that
+// holds at least one fluid node; tiles are listed once per geometry.  A warp processes a tile TW/32 nodes per lane, one
 // node after the other.  Every warp owns a private pipeline of kStages shared-memory
 // stages: stage s holds the Q population row windows of one tile (each window up to
 // TW + 16/sizeof(T) elements, start aligned down to 16 bytes), filled by bulk copies
